@@ -26,6 +26,7 @@ The primitives are non-normalised (Appendix A); coefficients are used as given.
 """
 import ctypes
 import os
+import platform
 import subprocess
 import sys
 
@@ -38,6 +39,9 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _lib = None
 
+MODES = {"double": 0, "extended": 1, "quad": 2}
+SPH_LMAX = 10
+
 
 def build(force=False):
     """Compile md3c.c with gcc + OpenMP into oracle/_build/liboracle.so."""
@@ -49,7 +53,10 @@ def build(force=False):
             return _SO
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _SO + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp] + src + ["-lm"]
+    libs = ["-lm"]
+    if platform.machine() in ("x86_64", "AMD64"):
+        libs = ["-lquadmath", "-lm"]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-o", tmp] + src + libs
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
@@ -65,9 +72,10 @@ def lib():
         f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
         L.oracle_boys.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, f64p]
         L.oracle_boys.restype = None
-        L.oracle_eri3c_cart.argtypes = [i32p, i32p, i64p, f64p, f64p, f64p,
-                                        ctypes.c_int64, i32p, i64p, f64p, ctypes.c_int]
-        L.oracle_eri3c_cart.restype = ctypes.c_int
+        L.oracle_eri3c.argtypes = [i32p, i32p, i64p, f64p, f64p, f64p, ctypes.c_int64, i32p, i64p, f64p,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, f64p, f64p, i64p]
+        L.oracle_eri3c.restype = ctypes.c_int
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -77,11 +85,35 @@ def num_threads():
     return int(lib().oracle_num_threads())
 
 
-def boys(mmax, T, extended=False):
+def _mode(mode, extended=False):
+    if extended:
+        return 1
+    return MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+def boys(mmax, T, extended=False, mode="double"):
     """[F_0(T), ..., F_mmax(T)] (Appendix A definition of the Boys function)."""
     out = np.zeros(mmax + 1)
-    lib().oracle_boys(int(mmax), float(T), int(bool(extended)), out)
+    lib().oracle_boys(int(mmax), float(T), _mode(mode, extended), out)
     return out
+
+
+_SPH = None
+
+
+def _sph_tables():
+    global _SPH
+    if _SPH is None:
+        from .solid import solid_matrix_hilo
+        his, los, off = [], [], [0]
+        for l in range(SPH_LMAX + 1):
+            h, lo_ = solid_matrix_hilo(l)
+            his.append(h.ravel())
+            los.append(lo_.ravel())
+            off.append(off[-1] + h.size)
+        _SPH = (np.ascontiguousarray(np.concatenate(his)), np.ascontiguousarray(np.concatenate(los)),
+                np.ascontiguousarray(np.array(off, np.int64)))
+    return _SPH
 
 
 # --------------------------------------------------------------------------
@@ -109,41 +141,56 @@ def _combined(*bases):
             cat(co, np.float64), base)
 
 
-def cart_blocks(tables, trip, extended=False):
-    """Cartesian contracted blocks for shell triples trip[n,3] of a combined table.
+def _dims(l, pure):
+    return nsph(l) if pure else ncart(l)
+
+
+def blocks(tables, trip, mode="double", bra_pure=False, ket_pure=True, dA=-1, dB=-1, dC=-1):
+    """Contracted blocks for shell triples trip[n,3] of a combined table.
 
     Returns (flat array, offsets, shapes)."""
     l, k, off, xyz, ex, co = tables
     trip = np.ascontiguousarray(np.asarray(trip, np.int32).reshape(-1, 3))
-    sizes = np.array([ncart(l[a]) * ncart(l[b]) * ncart(l[c]) for a, b, c in trip], np.int64)
+    shapes = [(_dims(int(l[a]), bra_pure), _dims(int(l[b]), bra_pure), _dims(int(l[c]), ket_pure))
+              for a, b, c in trip]
+    sizes = np.array([x * y * z for x, y, z in shapes], np.int64)
     offs = np.zeros(len(trip), np.int64)
     if len(trip):
         offs[1:] = np.cumsum(sizes)[:-1]
     out = np.zeros(int(sizes.sum()) if len(trip) else 0)
     if len(trip):
-        rc = lib().oracle_eri3c_cart(l, k, off, xyz, ex, co, len(trip), trip, offs, out,
-                                     int(bool(extended)))
+        hi, lo, soff = _sph_tables()
+        rc = lib().oracle_eri3c(l, k, off, xyz, ex, co, len(trip), trip, offs, out, _mode(mode),
+                                int(bool(bra_pure)), int(bool(ket_pure)), int(dA), int(dB), int(dC),
+                                SPH_LMAX + 1, hi, lo, soff)
         if rc != 0:
-            raise ValueError("oracle_eri3c_cart failed with %d" % rc)
-    return out, offs
+            raise ValueError("oracle_eri3c failed with %d" % rc)
+    return out, offs, shapes
 
 
-def eri3c(orb, aux, pairs, auxs, bra_pure=True, extended=False):
+def cart_blocks(tables, trip, extended=False):
+    """Cartesian bra and Cartesian (true) ket blocks (flat, offsets)."""
+    flat, offs, _ = blocks(tables, trip, mode=_mode("double", extended), bra_pure=False, ket_pure=False)
+    return flat, offs
+
+
+def eri3c(orb, aux, pairs, auxs, bra_pure=True, extended=False, mode="double", ket_route="hermite"):
     """(ab|C) blocks for every (pair, aux shell): array [npair, naux, nA, nB, nC].
 
-    The ket is always solid harmonic (Sec. 2.2, first design assumption); the
-    bra is Cartesian (the paper's target) unless bra_pure, in which case both
-    bra shells are projected with the same solid-harmonic matrices.  The class
-    must be homogeneous (one (la, lb, lc)).
+    The ket is always solid harmonic (Sec. 2.2, first design assumption): with
+    ket_route="hermite" it is expanded exactly (Hobson's theorem), with
+    ket_route="cartesian" true Cartesian kets are computed and projected (kept
+    for cross-checks).  The bra is Cartesian (the paper's target) unless
+    bra_pure.  The class must be homogeneous (one (la, lb, lc)).
     """
     pairs = np.asarray(pairs, np.int64).reshape(-1, 2)
     auxs = np.asarray(auxs, np.int64).reshape(-1)
     l, k, off, xyz, ex, co, base = _combined(orb, aux)
+    if len(pairs) == 0 or len(auxs) == 0:
+        return np.zeros((len(pairs), len(auxs), 0, 0, 0))
     la = {int(orb.l[p]) for p in pairs[:, 0]}
     lb = {int(orb.l[p]) for p in pairs[:, 1]}
     lc = {int(aux.l[q]) for q in auxs}
-    if len(pairs) == 0 or len(auxs) == 0:
-        return np.zeros((len(pairs), len(auxs), 0, 0, 0))
     if len(la) != 1 or len(lb) != 1 or len(lc) != 1:
         raise ValueError("eri3c needs one (la, lb, lc) class")
     la, lb, lc = la.pop(), lb.pop(), lc.pop()
@@ -151,15 +198,19 @@ def eri3c(orb, aux, pairs, auxs, bra_pure=True, extended=False):
     trip[:, :, 0] = pairs[:, 0, None]
     trip[:, :, 1] = pairs[:, 1, None]
     trip[:, :, 2] = auxs[None, :] + base[1]
-    flat, _ = cart_blocks((l, k, off, xyz, ex, co), trip.reshape(-1, 3), extended)
-    X = flat.reshape(len(pairs), len(auxs), ncart(la), ncart(lb), ncart(lc))
-    X = np.einsum("Cc,PQabc->PQabC", solid_matrix(lc), X)
-    if bra_pure:
-        X = np.einsum("Aa,Bb,PQabC->PQABC", solid_matrix(la), solid_matrix(lb), X)
-    return X
+    md = _mode(mode, extended)
+    if ket_route == "cartesian":
+        flat, _, _ = blocks((l, k, off, xyz, ex, co), trip.reshape(-1, 3), md, bra_pure=False, ket_pure=False)
+        X = flat.reshape(len(pairs), len(auxs), ncart(la), ncart(lb), ncart(lc))
+        X = np.einsum("Cc,PQabc->PQabC", solid_matrix(lc), X)
+        if bra_pure:
+            X = np.einsum("Aa,Bb,PQabC->PQABC", solid_matrix(la), solid_matrix(lb), X)
+        return X
+    flat, _, _ = blocks((l, k, off, xyz, ex, co), trip.reshape(-1, 3), md, bra_pure=bra_pure, ket_pure=True)
+    return flat.reshape(len(pairs), len(auxs), _dims(la, bra_pure), _dims(lb, bra_pure), nsph(lc))
 
 
-def eri3c_triples(orb, aux, trip_pairs, trip_aux, bra_pure=True, extended=False):
+def eri3c_triples(orb, aux, trip_pairs, trip_aux, bra_pure=True, extended=False, mode="double"):
     """(ab|C) for explicit triples (pair_i, aux_i), any mix of classes; list of arrays."""
     l, k, off, xyz, ex, co, base = _combined(orb, aux)
     trip_pairs = np.asarray(trip_pairs, np.int64).reshape(-1, 2)
@@ -168,17 +219,9 @@ def eri3c_triples(orb, aux, trip_pairs, trip_aux, bra_pure=True, extended=False)
     trip[:, 0] = trip_pairs[:, 0]
     trip[:, 1] = trip_pairs[:, 1]
     trip[:, 2] = trip_aux + base[1]
-    flat, offs = cart_blocks((l, k, off, xyz, ex, co), trip, extended)
-    out = []
-    for i, (a, b, c) in enumerate(trip):
-        la, lb, lc = int(l[a]), int(l[b]), int(l[c])
-        n = ncart(la) * ncart(lb) * ncart(lc)
-        X = flat[offs[i]:offs[i] + n].reshape(ncart(la), ncart(lb), ncart(lc))
-        X = np.einsum("Cc,abc->abC", solid_matrix(lc), X)
-        if bra_pure:
-            X = np.einsum("Aa,Bb,abC->ABC", solid_matrix(la), solid_matrix(lb), X)
-        out.append(X)
-    return out
+    flat, offs, shapes = blocks((l, k, off, xyz, ex, co), trip, _mode(mode, extended), bra_pure=bra_pure,
+                                ket_pure=True)
+    return [flat[o:o + a * b * c].reshape(a, b, c) for o, (a, b, c) in zip(offs, shapes)]
 
 
 # --------------------------------------------------------------------------
@@ -221,51 +264,13 @@ def dfj(orb, aux, D, c, tasks=None, extended=False):
 
 # --------------------------------------------------------------------------
 # Gradient of E = c^T gamma = sum_{mu nu P} D_{mu nu} c_P (mu nu|P)
-# with D and c held fixed.  Derivatives of a Cartesian primitive:
-#   d/dA_i phi_a = 2 zeta_a phi_{a+1_i} - a_i phi_{a-1_i}
-# (differentiate the definition in Appendix A), applied to all three centres
-# independently, so that sum of forces = 0 is a genuine check.
+# with D and c held fixed.  Each centre is differentiated independently in
+# md3c (d/dA_i phi_a = 2 zeta_a phi_{a+1_i} - a_i phi_{a-1_i} from the
+# definition in Appendix A; the solid-harmonic ket through its Hermite
+# expansion), so that the sum of forces vanishing is a genuine check.
 # --------------------------------------------------------------------------
 
-class _Shifted:
-    """Basis whose shells have l+shift and coefficients scaled by (2 zeta)^power."""
-
-    def __init__(self, b, shift, power):
-        self.l = np.asarray(b.l) + shift
-        self.k = np.asarray(b.k)
-        self.off = np.asarray(b.off)
-        self.xyz = np.asarray(b.xyz)
-        self.exps = np.asarray(b.exps)
-        self.coefs = np.asarray(b.coefs) * (2.0 * np.asarray(b.exps)) ** power
-
-
-def _cart_index(l):
-    return {c: i for i, c in enumerate(cart_list(l))}
-
-
-def _deriv_cart(plus, minus, l):
-    """d/dcentre of a Cartesian block along the last axis.
-
-    plus[..., nc(l+1)] holds (.|l+1) with 2zeta-weighted coefficients, minus
-    [..., nc(l-1)] the plain (.|l-1) (or None when l = 0).  Returns [3, ..., nc(l)].
-    """
-    ip = _cart_index(l + 1)
-    im = _cart_index(l - 1) if l > 0 else {}
-    shape = plus.shape[:-1] + (ncart(l),)
-    out = np.zeros((3,) + shape)
-    for j, c in enumerate(cart_list(l)):
-        for ax in range(3):
-            cp = list(c)
-            cp[ax] += 1
-            out[ax][..., j] += plus[..., ip[tuple(cp)]]
-            if c[ax] > 0:
-                cm = list(c)
-                cm[ax] -= 1
-                out[ax][..., j] -= c[ax] * minus[..., im[tuple(cm)]]
-    return out
-
-
-def dfj_grad(orb, aux, D, c, natom, tasks=None):
+def dfj_grad(orb, aux, D, c, natom, tasks=None, mode="double"):
     """dE/dR[natom, 3] for E = c^T gamma (pure orbital and aux bases)."""
     ao = ao_offsets(orb)
     aq = ao_offsets(aux)
@@ -273,39 +278,25 @@ def dfj_grad(orb, aux, D, c, natom, tasks=None):
     if tasks is None:
         tasks = [(i, j, P) for i in range(nsh) for j in range(i, nsh) for P in range(len(aux.l))]
     tasks = np.asarray(tasks, np.int64).reshape(-1, 3)
+    l, k, off, xyz, ex, co, base = _combined(orb, aux)
+    trip = np.empty((len(tasks), 3), np.int32)
+    trip[:, 0] = tasks[:, 0]
+    trip[:, 1] = tasks[:, 1]
+    trip[:, 2] = tasks[:, 2] + base[1]
     G = np.zeros((natom, 3))
-    orb_p, orb_m = _Shifted(orb, +1, 1), _Shifted(orb, -1, 0)
-    aux_p, aux_m = _Shifted(aux, +1, 1), _Shifted(aux, -1, 0)
+    W = []
     for (i, j, P) in tasks:
-        la, lb, lc = int(orb.l[i]), int(orb.l[j]), int(aux.l[P])
         w = 1.0 if i == j else 2.0
-        Dab = D[ao[i]:ao[i + 1], ao[j]:ao[j + 1]]
-        cP = c[aq[P]:aq[P + 1]]
-        W = w * np.einsum("AB,C->ABC", Dab, cP)
-        Ta, Tb, Tc = solid_matrix(la), solid_matrix(lb), solid_matrix(lc)
-
-        def cart(bA, sa, bB, sb, bC, sc):
-            l_, k_, off_, xyz_, ex_, co_, base = _combined(bA, bB, bC)
-            flat, _ = cart_blocks((l_, k_, off_, xyz_, ex_, co_),
-                                  np.array([[sa, sb + base[1], sc + base[2]]], np.int32))
-            return flat.reshape(ncart(int(l_[sa])), ncart(int(l_[sb + base[1]])),
-                                ncart(int(l_[sc + base[2]])))
-
-        # centre A
-        plus = cart(orb_p, i, orb, j, aux, P)                   # (a+1 b|c)
-        minus = cart(orb_m, i, orb, j, aux, P) if la > 0 else None
-        dA = _deriv_cart(np.moveaxis(plus, 0, -1), None if minus is None else np.moveaxis(minus, 0, -1), la)
-        dA = np.moveaxis(dA, -1, 1)                             # [3, a, b, c]
-        # centre B
-        plus = cart(orb, i, orb_p, j, aux, P)
-        minus = cart(orb, i, orb_m, j, aux, P) if lb > 0 else None
-        dB = _deriv_cart(np.moveaxis(plus, 1, -1), None if minus is None else np.moveaxis(minus, 1, -1), lb)
-        dB = np.moveaxis(dB, -1, 2)
-        # centre C
-        plus = cart(orb, i, orb, j, aux_p, P)
-        minus = cart(orb, i, orb, j, aux_m, P) if lc > 0 else None
-        dC = _deriv_cart(plus, minus, lc)
-        for d, atom in ((dA, orb.atom[i]), (dB, orb.atom[j]), (dC, aux.atom[P])):
-            sph = np.einsum("Aa,Bb,Cc,xabc->xABC", Ta, Tb, Tc, d)
-            G[int(atom)] += np.einsum("xABC,ABC->x", sph, W)
+        W.append(w * np.einsum("AB,C->ABC", D[ao[i]:ao[i + 1], ao[j]:ao[j + 1]], c[aq[P]:aq[P + 1]]))
+    for centre in range(3):
+        for axis in range(3):
+            d = [-1, -1, -1]
+            d[centre] = axis
+            flat, offs, shapes = blocks((l, k, off, xyz, ex, co), trip, mode, bra_pure=True, ket_pure=True,
+                                        dA=d[0], dB=d[1], dC=d[2])
+            for n, (i, j, P) in enumerate(tasks):
+                a_, b_, c_ = shapes[n]
+                blk = flat[offs[n]:offs[n] + a_ * b_ * c_].reshape(a_, b_, c_)
+                atom = (orb.atom[i], orb.atom[j], aux.atom[P])[centre]
+                G[int(atom), axis] += float(np.sum(blk * W[n]))
     return G

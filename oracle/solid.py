@@ -119,3 +119,27 @@ def nsph(l):
 
 def ncart(l):
     return (l + 1) * (l + 2) // 2
+
+
+@lru_cache(maxsize=None)
+def solid_matrix_hilo(l):
+    """(hi, lo) float64 matrices with hi + lo equal to T[m+l][c] to ~1e-32.
+
+    The exact value is sqrt(norm2) * rational; it is evaluated with 50-digit
+    decimal arithmetic and split into two doubles, so that the oracle's
+    extended and binary128 modes see the coefficients at their own precision."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 50
+    carts = cart_list(l)
+    idx = {c: i for i, c in enumerate(carts)}
+    hi = np.zeros((2 * l + 1, len(carts)))
+    lo = np.zeros((2 * l + 1, len(carts)))
+    for m in range(-l, l + 1):
+        poly, norm2 = solid_harmonic_poly(l, m)
+        s = (Decimal(norm2.numerator) / Decimal(norm2.denominator)).sqrt()
+        for key, c in poly.items():
+            v = s * Decimal(c.numerator) / Decimal(c.denominator)
+            h = float(v)
+            hi[m + l, idx[key]] = h
+            lo[m + l, idx[key]] = float(v - Decimal(h))
+    return hi, lo

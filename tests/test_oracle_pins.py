@@ -301,3 +301,58 @@ def test_solid_harmonics_orthogonal_on_sphere(l):
     S = solid_matrix(l) @ mono
     G = (S * wt) @ S.T
     np.testing.assert_allclose(G, 4 * np.pi / (2 * l + 1) * np.eye(2 * l + 1), atol=1e-13)
+
+
+# ------------------------------------------------------------------ solid-harmonic ket route
+def _ss_closed(p, ip, iq, l):
+    """(s s|C_lm) = pref K F_l(T) S_lm((rho/zc) PC): the one-term closed form
+    (VRR2 of Sec. 2.5.1 with a = 0 has no a_i term), F_l in binary128."""
+    a, b = p.pairs[ip]
+    c = p.auxs[iq]
+    A, B, C = p.orb.xyz[a], p.orb.xyz[b], p.aux.xyz[c]
+    za, zb, zc = p.orb.exps[p.orb.off[a]], p.orb.exps[p.orb.off[b]], p.aux.exps[p.aux.off[c]]
+    ca, cb, cc = p.orb.coefs[p.orb.off[a]], p.orb.coefs[p.orb.off[b]], p.aux.coefs[p.aux.off[c]]
+    g, P, rho, K, pref, T = _std(A, B, C, za, zb, zc)
+    X = rho / zc * (P - C)
+    Fl = oracle.boys(l, T, mode="quad")[l]
+    mono = np.array([X[0] ** e[0] * X[1] ** e[1] * X[2] ** e[2] for e in cart_list(l)])
+    return pref * K * ca * cb * cc * Fl * (solid_matrix(l) @ mono)
+
+
+@pytest.mark.parametrize("lc", [0, 1, 2, 4, 6])
+def test_ss_solid_ket_closed_form(lc):
+    """Includes compact kets far from the bra (T up to several hundred), where
+    projecting true Cartesian kets loses up to eight digits."""
+    p = W.class_problem(0, 0, lc, 5, 7, 1, 1, 1, box=6.0, exp_lo=0.1, exp_hi=50.0, seed=1006 + lc)
+    X = oracle.eri3c(p.orb, p.aux, p.pairs, p.auxs)
+    for ip in range(5):
+        for iq in range(7):
+            ref = _ss_closed(p, ip, iq, lc)
+            np.testing.assert_allclose(X[ip, iq, 0, 0], ref, rtol=0, atol=2e-14 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("la,lb,lc", [(1, 2, 3), (2, 2, 4), (3, 1, 6)])
+def test_ket_routes_agree_in_binary128(la, lb, lc):
+    """Hermite (Hobson) ket and projected Cartesian ket are the same integral."""
+    p = W.class_problem(la, lb, lc, 3, 4, 2, 1, 1, box=6.0, exp_lo=0.1, exp_hi=50.0, seed=41 + lc)
+    X = oracle.eri3c(p.orb, p.aux, p.pairs, p.auxs, bra_pure=False, mode="quad")
+    Y = oracle.eri3c(p.orb, p.aux, p.pairs, p.auxs, bra_pure=False, mode="quad", ket_route="cartesian")
+    s = np.abs(X).max(axis=(2, 3, 4), keepdims=True)
+    assert (np.abs(X - Y) / s).max() < 1e-9
+
+
+@pytest.mark.parametrize("la,lb,lc", [(2, 1, 2), (4, 4, 6), (3, 4, 3)])
+def test_precision_modes_agree(la, lb, lc):
+    p = W.class_problem(la, lb, lc, 2, 3, 2, 2, 1, box=6.0, exp_lo=0.1, exp_hi=50.0, seed=23 + la)
+    q = oracle.eri3c(p.orb, p.aux, p.pairs, p.auxs, mode="quad")
+    e = oracle.eri3c(p.orb, p.aux, p.pairs, p.auxs, mode="extended")
+    d = oracle.eri3c(p.orb, p.aux, p.pairs, p.auxs, mode="double")
+    s = np.abs(q).max(axis=(2, 3, 4), keepdims=True)
+    assert (np.abs(e - q) / s).max() < 1e-12
+    assert (np.abs(d - q) / s).max() < 1e-8
+
+
+def test_boys_quad_mode():
+    for T in [0.0, 0.7, 12.0, 29.9, 30.0, 85.0, 400.0]:
+        np.testing.assert_allclose(oracle.boys(24, T, mode="quad"), oracle.boys(24, T, mode="extended"),
+                                   rtol=3e-18, atol=0)
