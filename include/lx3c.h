@@ -1,0 +1,163 @@
+/*
+ * lx3c — 3-center Coulomb integrals (ab|C) and density-fitted Coulomb (DF-J)
+ * quantities on one NVIDIA GB300 (sm_103a), all arithmetic in FP64.
+ *
+ * Method: Asadchev & Valeev, "Memory-Efficient Recursive Evaluation of
+ * 3-Center Gaussian Integrals" (arXiv:2210.03192):
+ *   Boys function -> [00|0]^(m) (Sec. 2.5.2) -> VRR1 (Eq. vrr1) ->
+ *   early-contracted n-quantum CVRR2 (Sec. 2.5.4, Eqs. a0cv2/cVRR2) ->
+ *   Cartesian-to-solid-harmonic ket transform -> HRR (Eq. hrr),
+ *   and integral digestion into DF-J (Sec. 3): gamma_P = sum_ab (ab|P) D_ab,
+ *   J_ab = sum_P (ab|P) c_P.
+ *
+ * Conventions (all calls):
+ *   - Primitive Gaussians are NOT normalised (paper, Appendix A); contraction
+ *     coefficients are used exactly as given.
+ *   - Units: bohr.  Shell l <= LX3C_LMAX_ORB for orbital (bra) shells and
+ *     l <= LX3C_LMAX_AUX for auxiliary (ket) shells; at most LX3C_KMAX
+ *     primitives per shell.
+ *   - Cartesian order inside a shell: x descending, then y descending
+ *     (xx, xy, xz, yy, yz, zz).  Solid harmonics: real, Racah-normalised,
+ *     ordered m = -l..l (p: y, z, x); S_{l,0}(0,0,1) = 1.
+ *   - The ket shell is always solid harmonic.  The bra is solid harmonic when
+ *     bra_pure != 0 (each bra shell projected like the ket), else Cartesian.
+ *   - Integral block layout: out[pair][aux][A][B][C], C fastest, row-major,
+ *     FP64, pairs and aux shells in the caller's list order.
+ *   - Ownership: caller owns every data buffer it passes; the library owns
+ *     lx3c_basis / lx3c_plan objects, freed with the matching destroy call.
+ *   - Pointers marked "device" must be device (HBM) pointers of the current
+ *     device; "host" pointers are read (or written) before the call returns.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (0 = legacy default
+ *     stream).  Execute calls are asynchronous on that stream; *_create and
+ *     *_plan calls may synchronise.
+ *   - Errors: every call returns an lx3c_status; on failure nothing is
+ *     launched (input is validated on the host first) unless the status is
+ *     LX3C_ECUDA.  lx3c_last_error() returns a thread-local message.
+ */
+#ifndef LX3C_H
+#define LX3C_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int lx3c_status;
+#define LX3C_OK 0
+#define LX3C_EINVAL (-1)   /* malformed argument (null pointer, bad index, mixed class, ...) */
+#define LX3C_ENOTSUP (-2)  /* outside supported limits (l, K, shared-memory budget) */
+#define LX3C_ENOMEM (-3)   /* host or device allocation failed */
+#define LX3C_ECUDA (-4)    /* a CUDA runtime call failed */
+#define LX3C_EDEVICE (-5)  /* a kernel reported an error through its status word */
+
+#define LX3C_LMAX_ORB 6
+#define LX3C_LMAX_AUX 6
+#define LX3C_KMAX 16
+
+typedef struct lx3c_basis lx3c_basis;
+typedef struct lx3c_plan lx3c_plan;
+
+/* Thread-local description of the last failure in this thread. */
+const char* lx3c_last_error(void);
+
+/* Library version string. */
+const char* lx3c_version(void);
+
+/*
+ * Basis (shell table) — paper Appendix A (contracted Cartesian Gaussian shells).
+ *   nshell      number of shells (>= 0)
+ *   l[nshell]   angular momentum per shell (host)
+ *   k[nshell]   number of primitives per shell, 1..LX3C_KMAX (host)
+ *   xyz[3*nshell] centres, bohr (host)
+ *   atom[nshell] owning atom index (>= 0) or NULL (host); used by gradients
+ *   exps, coefs  primitive exponents (> 0, finite) and coefficients, shell-major,
+ *                sum(k) entries each (host)
+ * Copies everything to the device; returns LX3C_EINVAL on malformed input,
+ * LX3C_ENOTSUP if a shell exceeds the limits.
+ */
+lx3c_status lx3c_basis_create(lx3c_basis** out, int64_t nshell, const int32_t* l, const int32_t* k,
+                              const double* xyz, const int32_t* atom, const double* exps,
+                              const double* coefs, void* stream);
+void lx3c_basis_destroy(lx3c_basis* b);
+
+/*
+ * Plan for one homogeneous integral class (la, lb | lc), paper Sec. 2.5.1.
+ *   orb, aux      bases for the bra and the ket shells
+ *   pairs[2*npair] host list of (a, b) shell indices into orb; all pairs must
+ *                 share (l_a, k_a, l_b, k_b)
+ *   auxs[naux]    host list of ket shell indices into aux; all must share (l, k)
+ *   bra_pure      1: solid-harmonic bra, 0: Cartesian bra
+ * Builds the class recurrence tables, uploads the lists, and allocates the
+ * plan's device scratch (primitive-pair records).  Returns LX3C_EINVAL for an
+ * empty or mixed list or an index out of range.
+ */
+lx3c_status lx3c_eri3c_plan(lx3c_plan** out, const lx3c_basis* orb, const lx3c_basis* aux,
+                            const int32_t* pairs, int64_t npair, const int32_t* auxs, int64_t naux,
+                            int bra_pure, void* stream);
+
+/*
+ * Evaluate the plan's integrals into out (device, npair*naux*nA*nB*nC doubles,
+ * layout above).  Runs the primitive-pair precompute and the integral kernel
+ * on `stream`.
+ */
+lx3c_status lx3c_eri3c_execute(lx3c_plan* plan, double* out, void* stream);
+
+/* Size of one (pair, aux) block (nA*nB*nC) and the plan's total output length. */
+lx3c_status lx3c_plan_sizes(const lx3c_plan* plan, int64_t* block, int64_t* total);
+
+/*
+ * Launch shape of a plan (for benchmarks and diagnostics).  Writes up to n
+ * int64 values: [kernel launches per execute, then for each of the two
+ * orientations (recurrences on A, on B): sub-pairs, triples per tile T,
+ * primitive chunk G, lane mode, dynamic shared memory bytes, grid size].
+ */
+lx3c_status lx3c_plan_info(const lx3c_plan* plan, int64_t* out, int n);
+
+void lx3c_plan_destroy(lx3c_plan* plan);
+
+/*
+ * One-call host-buffer form of lx3c_eri3c_plan + lx3c_eri3c_execute: shell
+ * tables, lists and the output are host memory; device memory is allocated
+ * and freed inside the call, which synchronises `stream` before returning.
+ * out_host receives npair*naux*nA*nB*nC doubles.
+ */
+lx3c_status lx3c_eri3c_host(int64_t orb_nshell, const int32_t* orb_l, const int32_t* orb_k,
+                            const double* orb_xyz, const double* orb_exps, const double* orb_coefs,
+                            int64_t aux_nshell, const int32_t* aux_l, const int32_t* aux_k,
+                            const double* aux_xyz, const double* aux_exps, const double* aux_coefs,
+                            const int32_t* pairs, int64_t npair, const int32_t* auxs, int64_t naux,
+                            int bra_pure, double* out_host, void* stream);
+
+/*
+ * Boys function F_m(T) = int_0^1 y^{2m} exp(-T y^2) dy (Appendix A) on the
+ * device, by the same evaluator the integral kernels use (Sec. 2.5.2):
+ * out[i*(mmax+1) + m] = F_m(T[i]) for m = 0..mmax, 0 <= mmax <= 24.
+ * T (device, n values >= 0), out (device).
+ */
+lx3c_status lx3c_boys(const double* T, int64_t n, int mmax, double* out, void* stream);
+
+/*
+ * Algorithmic FP64 floating-point operations (FMA = 2) for one contracted
+ * (pair, aux) triple of class (la, lb | lc) with Kab primitive pairs and Kc
+ * ket primitives, counted on the FLOP-minimal form of the scheme.
+ */
+lx3c_status lx3c_class_flops(int la, int lb, int lc, int Kab, int Kc, int bra_pure, double* flops);
+
+/* Library's solid-harmonic matrix for shell l: out[(m+l)*ncart(l) + c]. */
+lx3c_status lx3c_solid_harmonics(int l, double* out);
+
+/*
+ * n-quantum CVRR2 expansion (Sec. 2.5.4) of the contracted target (a 0|c)
+ * as the library tabulates it: for bra exponents a[3], ket exponents c[3]
+ * writes up to cap terms (e[3], k, n[3], coef) into terms[8*i..8*i+7] as
+ * doubles and their count into *nterms.
+ */
+lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap, double* terms,
+                                 int32_t* nterms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LX3C_H */

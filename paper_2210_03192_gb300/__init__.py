@@ -1,1 +1,180 @@
-"""GB300-native 3-center Coulomb integrals and density-fitted J (arXiv:2210.03192 hot path)."""
+"""GB300-native 3-center Coulomb integrals (ab|C) and density-fitted J.
+
+Python face of the lx3c C-ABI library (include/lx3c.h).  Torch is used only
+for device memory and streams; every step of the integral path runs in the
+library's CUDA kernels.  Calls fail loudly (LibraryError) when the library or
+a GPU is missing: there is no CPU fallback.
+
+Main entry points:
+  DeviceBasis(basis)                    upload a shell table (workloads.Basis)
+  Eri3cPlan(orb, aux, pairs, auxs, bra_pure)   plan one (la lb|lc) class
+      .execute(out=None, stream=None) -> torch.cuda tensor [npair, naux, nA, nB, nC]
+  eri3c(orb, aux, pairs, auxs, bra_pure)       one-shot device evaluation
+  eri3c_host(orb, aux, pairs, auxs, bra_pure)  host arrays in, numpy out
+  boys(T, mmax)                          device Boys function (same evaluator)
+  class_flops(la, lb, lc, Kab, Kc, bra_pure)   algorithmic FP64 flops per triple
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import LibraryError, check, ptr
+from . import workloads  # noqa: F401  (seeded input generators)
+
+__all__ = ["DeviceBasis", "Eri3cPlan", "eri3c", "eri3c_host", "boys", "class_flops", "solid_harmonics",
+           "cvrr2_expansion", "LibraryError", "workloads"]
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise LibraryError("lx3c needs a CUDA device; none is available")
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class DeviceBasis:
+    """A basis uploaded to the current CUDA device (lx3c_basis)."""
+
+    def __init__(self, basis, stream=None):
+        L = _lib.load()
+        self.basis = basis
+        self.handle = ctypes.c_void_p()
+        l = np.ascontiguousarray(basis.l, np.int32)
+        k = np.ascontiguousarray(basis.k, np.int32)
+        xyz = np.ascontiguousarray(basis.xyz, np.float64)
+        atom = np.ascontiguousarray(basis.atom, np.int32) if getattr(basis, "atom", None) is not None else None
+        ex = np.ascontiguousarray(basis.exps, np.float64)
+        co = np.ascontiguousarray(basis.coefs, np.float64)
+        check(L.lx3c_basis_create(ctypes.byref(self.handle), len(l), ptr(l), ptr(k), ptr(xyz), ptr(atom), ptr(ex),
+                                  ptr(co), _stream_handle(stream)), "lx3c_basis_create")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.lx3c_basis_destroy(h)
+            self.handle = None
+
+
+class Eri3cPlan:
+    """Plan for one homogeneous (la lb|lc) class over pair and ket-shell lists."""
+
+    def __init__(self, orb, aux, pairs, auxs, bra_pure=True, stream=None):
+        L = _lib.load()
+        self.orb = orb if isinstance(orb, DeviceBasis) else DeviceBasis(orb, stream)
+        self.aux = aux if isinstance(aux, DeviceBasis) else DeviceBasis(aux, stream)
+        pairs = np.ascontiguousarray(np.asarray(pairs).reshape(-1, 2), np.int32)
+        auxs = np.ascontiguousarray(np.asarray(auxs).reshape(-1), np.int32)
+        self.npair, self.naux = len(pairs), len(auxs)
+        self.handle = ctypes.c_void_p()
+        check(L.lx3c_eri3c_plan(ctypes.byref(self.handle), self.orb.handle, self.aux.handle, ptr(pairs), len(pairs),
+                                ptr(auxs), len(auxs), int(bool(bra_pure)), _stream_handle(stream)),
+              "lx3c_eri3c_plan")
+        blk, tot = ctypes.c_int64(), ctypes.c_int64()
+        check(L.lx3c_plan_sizes(self.handle, ctypes.byref(blk), ctypes.byref(tot)), "lx3c_plan_sizes")
+        self.block, self.total = blk.value, tot.value
+        b = self.orb.basis
+        la, lb = int(b.l[pairs[0, 0]]), int(b.l[pairs[0, 1]])
+        lc = int(self.aux.basis.l[auxs[0]])
+        nA = (2 * la + 1) if bra_pure else (la + 1) * (la + 2) // 2
+        nB = (2 * lb + 1) if bra_pure else (lb + 1) * (lb + 2) // 2
+        self.shape = (self.npair, self.naux, nA, nB, 2 * lc + 1)
+        self.cls = (la, lb, lc)
+        info = np.zeros(13, np.int64)
+        check(L.lx3c_plan_info(self.handle, ptr(info), 13), "lx3c_plan_info")
+        self.launches = int(info[0])
+        self.shapes = [dict(nsub=int(info[1 + 6 * o]), T=int(info[2 + 6 * o]), G=int(info[3 + 6 * o]),
+                            mode=int(info[4 + 6 * o]), smem=int(info[5 + 6 * o]), grid=int(info[6 + 6 * o]))
+                       for o in range(2)]
+
+    def execute(self, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous() or out.numel() != self.total:
+            raise LibraryError("execute: out must be a contiguous float64 CUDA tensor with %d elements" % self.total)
+        check(_lib.load().lx3c_eri3c_execute(self.handle, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+              "lx3c_eri3c_execute")
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.lx3c_plan_destroy(h)
+            self.handle = None
+
+
+def eri3c(orb, aux, pairs, auxs, bra_pure=True, stream=None):
+    """(ab|C) for every (pair, ket shell): CUDA tensor [npair, naux, nA, nB, nC]."""
+    return Eri3cPlan(orb, aux, pairs, auxs, bra_pure, stream).execute(stream=stream)
+
+
+def eri3c_host(orb, aux, pairs, auxs, bra_pure=True, out=None, stream=None):
+    """Host-buffer path (lx3c_eri3c_host): numpy in, numpy out; copies inside the call."""
+    L = _lib.load()
+    pairs = np.ascontiguousarray(np.asarray(pairs).reshape(-1, 2), np.int32)
+    auxs = np.ascontiguousarray(np.asarray(auxs).reshape(-1), np.int32)
+    la, lb = int(orb.l[pairs[0, 0]]), int(orb.l[pairs[0, 1]])
+    lc = int(aux.l[auxs[0]])
+    nA = (2 * la + 1) if bra_pure else (la + 1) * (la + 2) // 2
+    nB = (2 * lb + 1) if bra_pure else (lb + 1) * (lb + 2) // 2
+    shape = (len(pairs), len(auxs), nA, nB, 2 * lc + 1)
+    if out is None:
+        out = np.empty(shape)
+    arrs = []
+
+    def a(x, dt):
+        x = np.ascontiguousarray(x, dt)
+        arrs.append(x)
+        return ptr(x)
+
+    st = _stream_handle(stream) if stream is not None else None
+    check(L.lx3c_eri3c_host(len(orb.l), a(orb.l, np.int32), a(orb.k, np.int32), a(orb.xyz, np.float64),
+                            a(orb.exps, np.float64), a(orb.coefs, np.float64), len(aux.l), a(aux.l, np.int32),
+                            a(aux.k, np.int32), a(aux.xyz, np.float64), a(aux.exps, np.float64),
+                            a(aux.coefs, np.float64), ptr(pairs), len(pairs), ptr(auxs), len(auxs),
+                            int(bool(bra_pure)), ptr(out), st), "lx3c_eri3c_host")
+    return out
+
+
+def boys(T, mmax, stream=None):
+    """F_0..F_mmax at the values of the CUDA float64 tensor T: tensor [n, mmax+1]."""
+    torch = _torch()
+    T = T.contiguous()
+    out = torch.empty((T.numel(), mmax + 1), dtype=torch.float64, device=T.device)
+    check(_lib.load().lx3c_boys(ctypes.c_void_p(T.data_ptr()), T.numel(), int(mmax), ctypes.c_void_p(out.data_ptr()),
+                                _stream_handle(stream)), "lx3c_boys")
+    return out
+
+
+def class_flops(la, lb, lc, Kab, Kc=1, bra_pure=True):
+    f = ctypes.c_double()
+    check(_lib.load().lx3c_class_flops(la, lb, lc, Kab, Kc, int(bool(bra_pure)), ctypes.byref(f)), "lx3c_class_flops")
+    return f.value
+
+
+def solid_harmonics(l):
+    nc = (l + 1) * (l + 2) // 2
+    out = np.zeros((2 * l + 1, nc))
+    check(_lib.load().lx3c_solid_harmonics(l, ptr(out)), "lx3c_solid_harmonics")
+    return out
+
+
+def cvrr2_expansion(a, c, cap=4096):
+    """Library's n-q CVRR2 expansion of (a 0|c): {((ex,ey,ez), k, (nx,ny,nz)): coef}."""
+    a = np.ascontiguousarray(a, np.int32)
+    c = np.ascontiguousarray(c, np.int32)
+    terms = np.zeros((cap, 8))
+    n = ctypes.c_int32()
+    check(_lib.load().lx3c_cvrr2_expansion(ptr(a), ptr(c), cap, ptr(terms), ctypes.byref(n)), "lx3c_cvrr2_expansion")
+    out = {}
+    for t in terms[:n.value]:
+        out[(tuple(int(x) for x in t[0:3]), int(t[3]), tuple(int(x) for x in t[4:7]))] = float(t[7])
+    return out

@@ -1,0 +1,86 @@
+"""ctypes binding of liblx3c.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module only loads
+the shared library, declares the C signatures of include/lx3c.h and converts
+arguments.  There is no CPU fallback: if the library cannot be loaded, every
+call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+c_i32p = ctypes.POINTER(ctypes.c_int32)
+c_f64p = ctypes.POINTER(ctypes.c_double)
+
+EXPORTS = {
+    # name: (restype, argtypes)
+    "lx3c_last_error": (ctypes.c_char_p, []),
+    "lx3c_version": (ctypes.c_char_p, []),
+    "lx3c_basis_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "lx3c_basis_destroy": (None, [ctypes.c_void_p]),
+    "lx3c_eri3c_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int, ctypes.c_void_p]),
+    "lx3c_eri3c_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lx3c_plan_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    "lx3c_plan_destroy": (None, [ctypes.c_void_p]),
+    "lx3c_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "lx3c_eri3c_host": (ctypes.c_int, [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int64] +
+                        [ctypes.c_void_p] * 5 + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "lx3c_boys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "lx3c_class_flops": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, c_f64p]),
+    "lx3c_solid_harmonics": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
+    "lx3c_cvrr2_expansion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_int32)]),
+}
+
+
+class LibraryError(RuntimeError):
+    pass
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load liblx3c.so (building it in-tree first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise LibraryError("liblx3c.so is not built (run paper_2210_03192_gb300.build.build())")
+    L = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in EXPORTS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(rc, what=""):
+    if rc != 0:
+        msg = load().lx3c_last_error()
+        raise LibraryError("%s failed (status %d): %s" % (what, rc, msg.decode() if msg else ""))
+
+
+def ptr(a):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()

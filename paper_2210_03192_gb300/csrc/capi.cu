@@ -1,0 +1,556 @@
+// C ABI of lx3c (declared in include/lx3c.h): basis and plan objects, input
+// validation, device-table management and launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lx3c.h"
+#include "lx3c_internal.h"
+
+namespace lx3c {
+cudaError_t init_constants();
+cudaError_t launch_pair_precompute(const DevBasis& orb, const int32_t* pairs, long long npair, int Ka, int Kb,
+                                   double* rec, double* ab, cudaStream_t st);
+cudaError_t launch_aux_precompute(const DevBasis& aux, const int32_t* auxs, long long naux, int Kc, double* rec,
+                                  double* cxyz, cudaStream_t st);
+cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st);
+cudaError_t launch_boys(const double* T, long long n, int mmax, const double* tab, const double* mid, double cL,
+                        double* out, cudaStream_t st);
+int eri3c_occupancy(int smem_bytes);
+}  // namespace lx3c
+
+using namespace lx3c;
+
+namespace {
+
+thread_local std::string g_err;
+
+lx3c_status fail(lx3c_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) return fail(LX3C_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Per-device constant data: Boys tables and uploaded class tables.
+struct DevClass {
+  void* blob = nullptr;
+  const uint4* vtab;
+  const int4* wtab;
+  const unsigned* atab;
+  const int* gptr;
+  const unsigned* gterm;
+  const int* gdst;
+  const double* pal;
+  const int* kptr;
+  const int2* kent;
+  const int4* htab;
+  const int* baptr;
+  const int2* baent;
+  const int* bbptr;
+  const int2* bbent;
+};
+
+struct DevState {
+  double* boys_tab = nullptr;
+  double* boys_mid = nullptr;
+  int nsm = 0;
+  int smem_per_sm = 0;
+  std::map<std::tuple<int, int, int, int>, DevClass> classes;
+};
+
+std::mutex g_mu;
+std::map<int, DevState> g_dev;
+
+lx3c_status device_state(DevState** out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevState& s = g_dev[dev];
+  if (!s.boys_tab) {
+    std::vector<double> tab, mid;
+    boys_tables(tab, mid);
+    CUDA_TRY(cudaMalloc(&s.boys_tab, tab.size() * 8));
+    CUDA_TRY(cudaMalloc(&s.boys_mid, mid.size() * 8));
+    CUDA_TRY(cudaMemcpy(s.boys_tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(s.boys_mid, mid.data(), mid.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(init_constants());
+    CUDA_TRY(cudaDeviceGetAttribute(&s.nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&s.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  }
+  *out = &s;
+  return LX3C_OK;
+}
+
+template <class T>
+size_t append(std::vector<char>& blob, const std::vector<T>& v) {
+  size_t off = (blob.size() + 15) & ~size_t(15);
+  blob.resize(off + v.size() * sizeof(T) + 16);
+  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+lx3c_status device_class(DevState* s, const ClassTables& ct, DevClass** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto key = std::make_tuple(ct.la, ct.lb, ct.lc, ct.bra_pure);
+  auto it = s->classes.find(key);
+  if (it != s->classes.end()) {
+    *out = &it->second;
+    return LX3C_OK;
+  }
+  std::vector<char> blob;
+  size_t o_v = append(blob, ct.vtab), o_w = append(blob, ct.wtab), o_a = append(blob, ct.atab),
+         o_gp = append(blob, ct.gptr), o_gt = append(blob, ct.gterm), o_gd = append(blob, ct.gdst),
+         o_pal = append(blob, ct.pal), o_kp = append(blob, ct.kptr), o_ke = append(blob, ct.kent),
+         o_h = append(blob, ct.htab), o_bap = append(blob, ct.baptr), o_bae = append(blob, ct.baent),
+         o_bbp = append(blob, ct.bbptr), o_bbe = append(blob, ct.bbent);
+  DevClass dc;
+  CUDA_TRY(cudaMalloc(&dc.blob, blob.size()));
+  CUDA_TRY(cudaMemcpy(dc.blob, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  char* b = (char*)dc.blob;
+  dc.vtab = (const uint4*)(b + o_v);
+  dc.wtab = (const int4*)(b + o_w);
+  dc.atab = (const unsigned*)(b + o_a);
+  dc.gptr = (const int*)(b + o_gp);
+  dc.gterm = (const unsigned*)(b + o_gt);
+  dc.gdst = (const int*)(b + o_gd);
+  dc.pal = (const double*)(b + o_pal);
+  dc.kptr = (const int*)(b + o_kp);
+  dc.kent = (const int2*)(b + o_ke);
+  dc.htab = (const int4*)(b + o_h);
+  dc.baptr = (const int*)(b + o_bap);
+  dc.baent = (const int2*)(b + o_bae);
+  dc.bbptr = (const int*)(b + o_bbp);
+  dc.bbent = (const int2*)(b + o_bbe);
+  auto r = s->classes.emplace(key, dc);
+  *out = &r.first->second;
+  return LX3C_OK;
+}
+
+}  // namespace
+
+struct lx3c_basis {
+  int64_t nshell = 0, nprim = 0;
+  std::vector<int32_t> l, k, atom;
+  std::vector<int64_t> off;
+  std::vector<double> xyz, exps, coefs;
+  int32_t* d_l = nullptr;
+  int32_t* d_k = nullptr;
+  int64_t* d_off = nullptr;
+  double* d_xyz = nullptr;
+  double* d_exps = nullptr;
+  double* d_coefs = nullptr;
+  DevBasis dev() const { return DevBasis{d_l, d_k, d_off, d_xyz, d_exps, d_coefs}; }
+};
+
+// One kernel launch of a plan: one orientation of the pair list.
+struct Launch {
+  ClassDesc desc;
+  int grid = 1;
+  long long nsub = 0;
+  int4* d_sub = nullptr;
+  int* d_prim = nullptr;
+};
+
+struct lx3c_plan {
+  const lx3c_basis* orb = nullptr;
+  const lx3c_basis* aux = nullptr;
+  int la = 0, lb = 0, lc = 0, bra_pure = 1;
+  int Ka = 1, Kb = 1, Kc = 1;
+  long long npair = 0, naux = 0;
+  int64_t nblk = 0;
+  Launch L[2];
+  int32_t* d_pairs = nullptr;
+  int32_t* d_auxs = nullptr;
+  double* d_pairrec = nullptr;
+  double* d_pairab = nullptr;
+  double* d_auxrec = nullptr;
+  double* d_auxc = nullptr;
+};
+
+extern "C" {
+
+const char* lx3c_last_error(void) { return g_err.c_str(); }
+
+const char* lx3c_version(void) { return "lx3c 0.1 (sm_103a, FP64)"; }
+
+void lx3c_basis_destroy(lx3c_basis* b) {
+  if (!b) return;
+  cudaFree(b->d_l);
+  cudaFree(b->d_k);
+  cudaFree(b->d_off);
+  cudaFree(b->d_xyz);
+  cudaFree(b->d_exps);
+  cudaFree(b->d_coefs);
+  delete b;
+}
+
+lx3c_status lx3c_basis_create(lx3c_basis** out, int64_t nshell, const int32_t* l, const int32_t* k,
+                              const double* xyz, const int32_t* atom, const double* exps, const double* coefs,
+                              void* stream) {
+  if (!out) return fail(LX3C_EINVAL, "basis_create: null output pointer");
+  *out = nullptr;
+  if (nshell < 0) return fail(LX3C_EINVAL, "basis_create: negative shell count");
+  if (nshell > 0 && (!l || !k || !xyz || !exps || !coefs)) return fail(LX3C_EINVAL, "basis_create: null array");
+  std::unique_ptr<lx3c_basis> b(new lx3c_basis);
+  b->nshell = nshell;
+  b->l.assign(l, l + nshell);
+  b->k.assign(k, k + nshell);
+  b->off.resize(nshell);
+  b->atom.assign(nshell, -1);
+  if (atom) b->atom.assign(atom, atom + nshell);
+  int64_t np = 0;
+  for (int64_t s = 0; s < nshell; ++s) {
+    if (l[s] < 0 || l[s] > std::max(LX3C_LMAX_ORB, LX3C_LMAX_AUX))
+      return fail(LX3C_ENOTSUP, "basis_create: shell " + std::to_string(s) + " has unsupported l");
+    if (k[s] < 1 || k[s] > LX3C_KMAX)
+      return fail(LX3C_ENOTSUP, "basis_create: shell " + std::to_string(s) + " has unsupported K");
+    b->off[s] = np;
+    np += k[s];
+  }
+  b->nprim = np;
+  b->xyz.assign(xyz, xyz + 3 * nshell);
+  b->exps.assign(exps, exps + np);
+  b->coefs.assign(coefs, coefs + np);
+  for (int64_t i = 0; i < 3 * nshell; ++i)
+    if (!std::isfinite(b->xyz[i])) return fail(LX3C_EINVAL, "basis_create: non-finite centre");
+  for (int64_t i = 0; i < np; ++i) {
+    if (!(b->exps[i] > 0.0) || !std::isfinite(b->exps[i]))
+      return fail(LX3C_EINVAL, "basis_create: exponent must be finite and > 0");
+    if (!std::isfinite(b->coefs[i])) return fail(LX3C_EINVAL, "basis_create: non-finite coefficient");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t n = (size_t)std::max<int64_t>(nshell, 1), npp = (size_t)std::max<int64_t>(np, 1);
+  CUDA_TRY(cudaMalloc(&b->d_l, n * 4));
+  CUDA_TRY(cudaMalloc(&b->d_k, n * 4));
+  CUDA_TRY(cudaMalloc(&b->d_off, n * 8));
+  CUDA_TRY(cudaMalloc(&b->d_xyz, n * 24));
+  CUDA_TRY(cudaMalloc(&b->d_exps, npp * 8));
+  CUDA_TRY(cudaMalloc(&b->d_coefs, npp * 8));
+  if (nshell > 0) {
+    CUDA_TRY(cudaMemcpyAsync(b->d_l, b->l.data(), nshell * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b->d_k, b->k.data(), nshell * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b->d_off, b->off.data(), nshell * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b->d_xyz, b->xyz.data(), nshell * 24, cudaMemcpyHostToDevice, st));
+  }
+  if (np > 0) {
+    CUDA_TRY(cudaMemcpyAsync(b->d_exps, b->exps.data(), np * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b->d_coefs, b->coefs.data(), np * 8, cudaMemcpyHostToDevice, st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  *out = b.release();
+  return LX3C_OK;
+}
+
+void lx3c_plan_destroy(lx3c_plan* p) {
+  if (!p) return;
+  cudaFree(p->d_pairs);
+  cudaFree(p->d_auxs);
+  cudaFree(p->d_pairrec);
+  cudaFree(p->d_pairab);
+  cudaFree(p->d_auxrec);
+  cudaFree(p->d_auxc);
+  for (auto& l : p->L) {
+    cudaFree(l.d_sub);
+    cudaFree(l.d_prim);
+  }
+  delete p;
+}
+
+namespace {
+
+// Fill one launch descriptor for class (l1, l2 | lc) over a sub-pair list.
+lx3c_status make_launch(DevState* ds, lx3c_plan* p, int orient, const std::vector<int4>& sub,
+                        const std::vector<int>& prim, int kmax, cudaStream_t st) {
+  Launch& L = p->L[orient];
+  L.nsub = (long long)sub.size();
+  if (L.nsub == 0) return LX3C_OK;
+  const int l1 = orient ? p->lb : p->la, l2 = orient ? p->la : p->lb;
+  const ClassTables* ct;
+  try {
+    ct = &class_tables(l1, l2, p->lc, p->bra_pure);
+  } catch (std::exception& e) {
+    return fail(LX3C_ENOTSUP, std::string("eri3c_plan: ") + e.what());
+  }
+  DevClass* dc;
+  lx3c_status rc = device_class(ds, *ct, &dc);
+  if (rc) return rc;
+  LaunchShape sh = choose_shape(*ct, kmax, p->Kc, p->naux, ds->smem_per_sm);
+  if (sh.smem_bytes < 0 || sh.smem_bytes > 232448)
+    return fail(LX3C_ENOTSUP, "eri3c_plan: class does not fit in shared memory");
+  ClassDesc& d = L.desc;
+  std::memset(&d, 0, sizeof(d));
+  d.la = l1; d.lb = l2; d.lc = p->lc; d.Lab = l1 + l2; d.L = l1 + l2 + p->lc; d.bra_pure = p->bra_pure;
+  d.ncA = ct->ncA; d.ncB = ct->ncB; d.ncc = ct->ncc;
+  d.nA = ct->nA; d.nB = ct->nB; d.nC = ct->nC; d.nblk = d.nA * d.nB * d.nC;
+  d.orient = orient;
+  d.onA = orient ? ct->nB : ct->nA;
+  d.onB = orient ? ct->nA : ct->nB;
+  d.Kab = kmax; d.Kc = p->Kc; d.K = kmax * p->Kc;
+  d.Kab_rec = p->Ka * p->Kb;
+  d.NV = ct->NV; d.NW = ct->NW; d.NF = ct->NF; d.NACC = ct->NACC;
+  for (int e = 0; e <= d.Lab; ++e) d.vlev_start[e] = ct->vlev_start[e];
+  d.nW = ct->NW;
+  d.ngt = ct->nkrow * ct->ncc;
+  d.nkrow = ct->nkrow;
+  for (int j = 0; j <= l2; ++j) d.hrows[j] = ct->hrows[j];
+  for (int j = 0; j <= l2 + 1; ++j) d.hstart[j] = ct->hstart[j];
+  d.nbA = ct->nbA; d.nbB = ct->nbB;
+  d.vtab = dc->vtab; d.wtab = dc->wtab; d.atab = dc->atab; d.gptr = dc->gptr; d.gterm = dc->gterm;
+  d.gdst = dc->gdst; d.pal = dc->pal; d.kptr = dc->kptr; d.kent = dc->kent; d.htab = dc->htab;
+  d.baptr = dc->baptr; d.baent = dc->baent; d.bbptr = dc->bbptr; d.bbent = dc->bbent;
+  d.boys_tab = ds->boys_tab; d.boys_mid = ds->boys_mid; d.boys_cL = boys_large_const(d.L);
+  d.npair = p->npair; d.naux = p->naux;
+  fill_layout(d, *ct, sh);
+  d.nchunk = (d.K + d.G - 1) / d.G;
+  d.ntile_aux = (int)((p->naux + d.T - 1) / d.T);
+  d.nsub = L.nsub;
+  d.ntiles = L.nsub * d.ntile_aux;
+  int occ = eri3c_occupancy(d.smem_doubles * 8);
+  L.grid = (int)std::min<long long>(d.ntiles, (long long)ds->nsm * occ * 8);
+  CUDA_TRY(cudaMalloc(&L.d_sub, sub.size() * sizeof(int4)));
+  CUDA_TRY(cudaMalloc(&L.d_prim, std::max<size_t>(prim.size(), 1) * sizeof(int)));
+  CUDA_TRY(cudaMemcpyAsync(L.d_sub, sub.data(), sub.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+  if (!prim.empty())
+    CUDA_TRY(cudaMemcpyAsync(L.d_prim, prim.data(), prim.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  d.subpairs = L.d_sub;
+  d.primidx = L.d_prim;
+  return LX3C_OK;
+}
+
+}  // namespace
+
+lx3c_status lx3c_eri3c_plan(lx3c_plan** out, const lx3c_basis* orb, const lx3c_basis* aux, const int32_t* pairs,
+                            int64_t npair, const int32_t* auxs, int64_t naux, int bra_pure, void* stream) {
+  if (!out) return fail(LX3C_EINVAL, "eri3c_plan: null output pointer");
+  *out = nullptr;
+  if (!orb || !aux) return fail(LX3C_EINVAL, "eri3c_plan: null basis");
+  if (npair <= 0 || naux <= 0) return fail(LX3C_EINVAL, "eri3c_plan: empty pair or aux list");
+  if (!pairs || !auxs) return fail(LX3C_EINVAL, "eri3c_plan: null list");
+  if (npair > (1LL << 31) - 1 || naux > (1LL << 31) - 1) return fail(LX3C_ENOTSUP, "eri3c_plan: list too long");
+  int la = -1, lb = -1, lc = -1, Ka = 0, Kb = 0, Kc = 0;
+  for (int64_t i = 0; i < npair; ++i) {
+    int32_t a = pairs[2 * i], b = pairs[2 * i + 1];
+    if (a < 0 || a >= orb->nshell || b < 0 || b >= orb->nshell)
+      return fail(LX3C_EINVAL, "eri3c_plan: pair " + std::to_string(i) + " index out of range");
+    if (i == 0) { la = orb->l[a]; lb = orb->l[b]; Ka = orb->k[a]; Kb = orb->k[b]; }
+    if (orb->l[a] != la || orb->l[b] != lb || orb->k[a] != Ka || orb->k[b] != Kb)
+      return fail(LX3C_EINVAL, "eri3c_plan: mixed (l, K) in pair list at " + std::to_string(i));
+  }
+  for (int64_t i = 0; i < naux; ++i) {
+    int32_t c = auxs[i];
+    if (c < 0 || c >= aux->nshell) return fail(LX3C_EINVAL, "eri3c_plan: aux index out of range");
+    if (i == 0) { lc = aux->l[c]; Kc = aux->k[c]; }
+    if (aux->l[c] != lc || aux->k[c] != Kc) return fail(LX3C_EINVAL, "eri3c_plan: mixed (l, K) in aux list");
+  }
+  if (la > LX3C_LMAX_ORB || lb > LX3C_LMAX_ORB || lc > LX3C_LMAX_AUX)
+    return fail(LX3C_ENOTSUP, "eri3c_plan: angular momentum beyond the supported limits");
+  DevState* ds;
+  lx3c_status rc = device_state(&ds);
+  if (rc) return rc;
+  std::unique_ptr<lx3c_plan> p(new lx3c_plan);
+  p->orb = orb;
+  p->aux = aux;
+  p->la = la; p->lb = lb; p->lc = lc; p->bra_pure = bra_pure ? 1 : 0;
+  p->Ka = Ka; p->Kb = Kb; p->Kc = Kc;
+  p->npair = npair; p->naux = naux;
+  {
+    const ClassTables& ct = class_tables(la, lb, lc, p->bra_pure);
+    p->nblk = (int64_t)ct.nA * ct.nB * ct.nC;
+  }
+  // Orientation of every primitive pair: the recurrences run on the more
+  // compact centre (larger exponent), so that HRR transfers quanta towards
+  // the centre farther from P and never cancels (diffuse A with compact B
+  // would otherwise lose up to all FP64 digits).  Without HRR (lb = 0) every
+  // primitive pair keeps the caller's orientation.
+  std::vector<int4> subA, subB;
+  std::vector<int> primA, primB;
+  int kA = 0, kB = 0;
+  for (int64_t i = 0; i < npair; ++i) {
+    int32_t a = pairs[2 * i], b = pairs[2 * i + 1];
+    int oa = (int)primA.size(), ob = (int)primB.size();
+    for (int ia = 0; ia < Ka; ++ia)
+      for (int ib = 0; ib < Kb; ++ib) {
+        double za = orb->exps[orb->off[a] + ia], zb = orb->exps[orb->off[b] + ib];
+        bool onB = lb > 0 && zb > za;
+        (onB ? primB : primA).push_back(ia * Kb + ib);
+      }
+    int na = (int)primA.size() - oa, nb = (int)primB.size() - ob;
+    if (na) subA.push_back(int4{(int)i, oa, na, 0});
+    if (nb) subB.push_back(int4{(int)i, ob, nb, na > 0 ? 1 : 0});
+    kA = std::max(kA, na);
+    kB = std::max(kB, nb);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = make_launch(ds, p.get(), 0, subA, primA, kA, st);
+  if (!rc) rc = make_launch(ds, p.get(), 1, subB, primB, kB, st);
+  if (rc) return rc;
+  const int Kab = Ka * Kb;
+  CUDA_TRY(cudaMalloc(&p->d_pairs, npair * 8));
+  CUDA_TRY(cudaMalloc(&p->d_auxs, naux * 4));
+  CUDA_TRY(cudaMalloc(&p->d_pairrec, (size_t)npair * Kab * kPairRec * 8));
+  CUDA_TRY(cudaMalloc(&p->d_pairab, (size_t)npair * 3 * 8));
+  CUDA_TRY(cudaMalloc(&p->d_auxrec, (size_t)naux * Kc * kAuxRec * 8));
+  CUDA_TRY(cudaMalloc(&p->d_auxc, (size_t)naux * 3 * 8));
+  CUDA_TRY(cudaMemcpyAsync(p->d_pairs, pairs, npair * 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(p->d_auxs, auxs, naux * 4, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (auto& L : p->L) {
+    L.desc.pairrec = p->d_pairrec; L.desc.pairab = p->d_pairab;
+    L.desc.auxrec = p->d_auxrec; L.desc.auxc = p->d_auxc;
+  }
+  *out = p.release();
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_eri3c_execute(lx3c_plan* p, double* out, void* stream) {
+  if (!p) return fail(LX3C_EINVAL, "eri3c_execute: null plan");
+  if (!out) return fail(LX3C_EINVAL, "eri3c_execute: null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(launch_pair_precompute(p->orb->dev(), p->d_pairs, p->npair, p->Ka, p->Kb, p->d_pairrec, p->d_pairab, st));
+  CUDA_TRY(launch_aux_precompute(p->aux->dev(), p->d_auxs, p->naux, p->Kc, p->d_auxrec, p->d_auxc, st));
+  for (auto& L : p->L) {
+    if (!L.nsub) continue;
+    ClassDesc d = L.desc;
+    d.out = out;
+    CUDA_TRY(launch_eri3c(d, L.grid, st));
+  }
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_plan_info(const lx3c_plan* p, int64_t* out, int n) {
+  if (!p || (!out && n > 0)) return fail(LX3C_EINVAL, "plan_info: null pointer");
+  std::vector<int64_t> v;
+  v.push_back(2 + (p->L[0].nsub > 0) + (p->L[1].nsub > 0));
+  for (auto& l : p->L) {
+    v.push_back(l.nsub);
+    v.push_back(l.desc.T);
+    v.push_back(l.desc.G);
+    v.push_back(l.desc.mode);
+    v.push_back((int64_t)l.desc.smem_doubles * 8);
+    v.push_back(l.grid);
+  }
+  for (int i = 0; i < n && i < (int)v.size(); ++i) out[i] = v[i];
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_plan_sizes(const lx3c_plan* p, int64_t* block, int64_t* total) {
+  if (!p) return fail(LX3C_EINVAL, "plan_sizes: null plan");
+  if (block) *block = p->nblk;
+  if (total) *total = (int64_t)p->npair * p->naux * p->nblk;
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_eri3c_host(int64_t orb_nshell, const int32_t* orb_l, const int32_t* orb_k, const double* orb_xyz,
+                            const double* orb_exps, const double* orb_coefs, int64_t aux_nshell,
+                            const int32_t* aux_l, const int32_t* aux_k, const double* aux_xyz,
+                            const double* aux_exps, const double* aux_coefs, const int32_t* pairs, int64_t npair,
+                            const int32_t* auxs, int64_t naux, int bra_pure, double* out_host, void* stream) {
+  if (!out_host) return fail(LX3C_EINVAL, "eri3c_host: null output");
+  lx3c_basis *orb = nullptr, *aux = nullptr;
+  lx3c_plan* plan = nullptr;
+  double* d_out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  lx3c_status rc = lx3c_basis_create(&orb, orb_nshell, orb_l, orb_k, orb_xyz, nullptr, orb_exps, orb_coefs, stream);
+  if (!rc) rc = lx3c_basis_create(&aux, aux_nshell, aux_l, aux_k, aux_xyz, nullptr, aux_exps, aux_coefs, stream);
+  if (!rc) rc = lx3c_eri3c_plan(&plan, orb, aux, pairs, npair, auxs, naux, bra_pure, stream);
+  int64_t total = 0;
+  if (!rc) rc = lx3c_plan_sizes(plan, nullptr, &total);
+  if (!rc) {
+    cudaError_t e = cudaMalloc(&d_out, (size_t)total * 8);
+    if (e != cudaSuccess) rc = fail(LX3C_ENOMEM, "eri3c_host: device output allocation failed");
+  }
+  if (!rc) rc = lx3c_eri3c_execute(plan, d_out, stream);
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(out_host, d_out, (size_t)total * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = fail(LX3C_ECUDA, std::string("eri3c_host: ") + cudaGetErrorString(e));
+  }
+  cudaFree(d_out);
+  lx3c_plan_destroy(plan);
+  lx3c_basis_destroy(orb);
+  lx3c_basis_destroy(aux);
+  return rc;
+}
+
+lx3c_status lx3c_boys(const double* T, int64_t n, int mmax, double* out, void* stream) {
+  if (n < 0 || mmax < 0 || mmax > kBoysMmax) return fail(LX3C_EINVAL, "boys: bad n or mmax");
+  if (n > 0 && (!T || !out)) return fail(LX3C_EINVAL, "boys: null pointer");
+  DevState* ds;
+  lx3c_status rc = device_state(&ds);
+  if (rc) return rc;
+  CUDA_TRY(launch_boys(T, n, mmax, ds->boys_tab, ds->boys_mid, boys_large_const(mmax), out, (cudaStream_t)stream));
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_class_flops(int la, int lb, int lc, int Kab, int Kc, int bra_pure, double* flops) {
+  if (!flops || la < 0 || lb < 0 || lc < 0 || la > LX3C_LMAX_ORB || lb > LX3C_LMAX_ORB || lc > LX3C_LMAX_AUX ||
+      Kab < 1 || Kc < 1)
+    return fail(LX3C_EINVAL, "class_flops: bad argument");
+  try {
+    const ClassTables& ct = class_tables(la, lb, lc, bra_pure ? 1 : 0);
+    *flops = ct.flops_prim * (double)Kab * Kc + ct.flops_contr;
+  } catch (std::exception& e) {
+    return fail(LX3C_ENOTSUP, e.what());
+  }
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_solid_harmonics(int l, double* out) {
+  if (l < 0 || l > 12 || !out) return fail(LX3C_EINVAL, "solid_harmonics: bad argument");
+  auto T = solid_matrix(l);
+  std::memcpy(out, T.data(), T.size() * 8);
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap, double* terms, int32_t* nterms) {
+  if (!a || !c || !nterms || (cap > 0 && !terms)) return fail(LX3C_EINVAL, "cvrr2_expansion: null pointer");
+  for (int i = 0; i < 3; ++i)
+    if (a[i] < 0 || c[i] < 0) return fail(LX3C_EINVAL, "cvrr2_expansion: negative exponent");
+  int la = a[0] + a[1] + a[2], lc = c[0] + c[1] + c[2];
+  if (la > 2 * LX3C_LMAX_ORB || lc > LX3C_LMAX_AUX) return fail(LX3C_ENOTSUP, "cvrr2_expansion: too large");
+  // the class (la, 0 | lc) contains the target (a 0|c) at level 0
+  const ClassTables* ct;
+  try {
+    ct = &class_tables(la, 0, lc, 0);
+  } catch (std::exception& e) {
+    return fail(LX3C_ENOTSUP, e.what());
+  }
+  int row = cart_index(a[0], a[1], a[2]);
+  int id = row * ct->ncc + cart_index(c[0], c[1], c[2]);
+  int q0 = ct->gptr[id], q1 = ct->gptr[id + 1];
+  *nterms = q1 - q0;
+  for (int q = q0; q < q1 && q - q0 < cap; ++q) {
+    unsigned e = ct->gterm[q];
+    const int4 key = ct->acc_key[e & 0xFFFFF];
+    int el = key.x >> 16, ei = key.x & 0xFFFF, nl = key.z >> 16, ni = key.z & 0xFFFF;
+    // decode component indices back to exponents
+    auto decode = [](int l, int idx, double* o) {
+      int i = 0;
+      for (int x = l; x >= 0; --x)
+        for (int y = l - x; y >= 0; --y) {
+          if (i == idx) { o[0] = x; o[1] = y; o[2] = l - x - y; return; }
+          ++i;
+        }
+    };
+    double* t = terms + 8 * (q - q0);
+    decode(el, ei, t);
+    t[3] = key.y;
+    decode(nl, ni, t + 4);
+    t[7] = ct->pal[e >> 20];
+  }
+  return LX3C_OK;
+}
+
+}  // extern "C"

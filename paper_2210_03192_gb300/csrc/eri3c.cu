@@ -1,0 +1,583 @@
+// Device kernels for contracted 3-center Coulomb integrals (ab|C)
+// (arXiv:2210.03192, HGPA scheme of Sec. 2.5.1):
+//   pair_precompute  primitive-pair quantities gamma, P, PA, K_ab (Appendix A)
+//   aux_precompute   ket primitive records
+//   eri3c_kernel     per tile of (one pair, T ket shells):
+//                      [00|0]^(m) from the Boys function       Sec. 2.5.2
+//                      VRR1                                      Eq. vrr1
+//                      CVRR2 prerequisites, contracted early     Eq. a0cv2 / Sec. 2.5.4
+//                      CVRR2 targets (n-quantum form)            Sec. 2.5.4
+//                      Cartesian -> solid-harmonic ket           Sec. 2.5.1
+//                      HRR                                       Eq. hrr
+//                      optional solid-harmonic bra, store
+//
+// GB300 design notes.  FP64 is the only scarce resource on this part (about
+// 2 DFMA per clock per SM against 128 FFMA), so every stage is written to
+// issue only the FP64 operations of the FLOP-minimal scheme with all 32 lanes
+// busy, while index decoding, shared-memory traffic and table reads (integer,
+// load/store pipes) hide under the FP64 pipe.  Each stage is a flat loop over
+// (triple, target) items driven by host-built tables; the triple index is the
+// fastest lane index when a tile holds >= 32 triples (warp-uniform table
+// entries, conflict-free strided shared memory) and the target index otherwise.
+// Primitive contraction happens in shared-memory accumulators (Eq. a0cv2
+// prerequisites), so no intermediate CVRR2 value is ever stored to global
+// memory and no atomics are needed.
+#include <cuda_runtime.h>
+
+#include "lx3c_internal.h"
+
+namespace lx3c {
+
+__constant__ double c_inv2m1[32];  // 1/(2m+1)
+
+struct FDiv {
+  unsigned d, m;
+  __device__ __forceinline__ void init(unsigned dd) {
+    d = dd;
+    m = (dd <= 1u) ? 0u : (0xFFFFFFFFu / dd + 1u);
+  }
+  // exact for n * d < 2^32
+  __device__ __forceinline__ unsigned div(unsigned n) const { return d <= 1u ? n : __umulhi(n, m); }
+};
+
+// 1/sqrt(x) for x > 0 in FP64: single-precision seed, then one Newton-Raphson
+// step carrying the second-order term (y1 = y0 (1 + e/2 + 3e^2/8),
+// e = 1 - x y0^2), which takes the ~1e-7 seed error to FP64 rounding level
+// with five FP64 operations.
+__device__ __forceinline__ double rsqrt_fp64(double x) {
+  float xf = __double2float_rn(x);
+  double y0 = (double)rsqrtf(xf);
+  double t = x * y0;
+  double e = fma(-t, y0, 1.0);
+  double p = fma(e, 0.375, 0.5);
+  double q = y0 * e;
+  return fma(q, p, y0);
+}
+
+// pref * F_m(T) for m = hi down to lo, written to v[(m - lo) * stride].
+// F_hi and exp(-T) come from the interpolation table (T < 117) or the
+// asymptotic form (T >= 117, exp(-T) = 0); lower orders by the downward
+// relation (2m+1) F_m = 2T F_{m+1} + exp(-T).
+__device__ __forceinline__ void boys_scaled(const double* __restrict__ tab, const double* __restrict__ mid,
+                                            double cL, int hi, int lo, double T, double pref, double* v,
+                                            int stride) {
+  double FL, ex;
+  if (T < kBoysTMax) {
+    int i = __float2int_rz(__double2float_rz(T) * (float)kBoysPerUnit);
+    i = min(max(i, 0), kBoysNInt - 1);
+    double dx = T - __ldg(mid + i);
+    const double* c = tab + ((size_t)i * kBoysNF + hi) * 8;
+    const double* ce = tab + ((size_t)i * kBoysNF + (kBoysNF - 1)) * 8;
+    FL = __ldg(c + 7);
+    ex = __ldg(ce + 7);
+#pragma unroll
+    for (int j = 6; j >= 0; --j) {
+      FL = fma(FL, dx, __ldg(c + j));
+      ex = fma(ex, dx, __ldg(ce + j));
+    }
+  } else {
+    double rs = rsqrt_fp64(T);
+    double b = rs * rs;
+    double p = rs;
+    int e = hi;
+    while (e) {
+      if (e & 1) p *= b;
+      e >>= 1;
+      if (e) b *= b;
+    }
+    FL = cL * p;
+    ex = 0.0;
+  }
+  double G = pref * FL;
+  double E = pref * ex;
+  double T2 = T + T;
+  v[(hi - lo) * stride] = G;
+  for (int m = hi - 1; m >= lo; --m) {
+    G = fma(T2, G, E) * c_inv2m1[m];
+    v[(m - lo) * stride] = G;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// precompute kernels
+// ---------------------------------------------------------------------------
+
+
+// One thread per primitive pair (pair p, a-primitive ia, b-primitive ib).
+__global__ void pair_precompute(DevBasis orb, const int32_t* __restrict__ pairs, long long npair, int Ka, int Kb,
+                                double* __restrict__ rec, double* __restrict__ ab) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long n = npair * Ka * Kb;
+  if (i >= n) return;
+  long long p = i / (Ka * Kb);
+  int r = (int)(i - p * Ka * Kb);
+  int ia = r / Kb, ib = r - ia * Kb;
+  int sa = pairs[2 * p], sb = pairs[2 * p + 1];
+  const double* A = orb.xyz + 3 * sa;
+  const double* B = orb.xyz + 3 * sb;
+  double za = orb.exps[orb.off[sa] + ia], ca = orb.coefs[orb.off[sa] + ia];
+  double zb = orb.exps[orb.off[sb] + ib], cb = orb.coefs[orb.off[sb] + ib];
+  double g = za + zb, ig = 1.0 / g;
+  double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
+  double ab2 = AB[0] * AB[0] + AB[1] * AB[1] + AB[2] * AB[2];
+  const double two_pi52 = 34.98683665524972;  // 2 pi^{5/2}
+  double* o = rec + i * kPairRec;
+  o[PR_G] = g;
+  o[PR_K] = ca * cb * exp(-za * zb * ig * ab2) * two_pi52 * ig;
+  for (int x = 0; x < 3; ++x) {
+    double P = (za * A[x] + zb * B[x]) * ig;
+    o[PR_P + x] = P;
+    o[PR_PA + x] = P - A[x];
+  }
+  for (int x = 0; x < 3; ++x) o[PR_PB + x] = o[PR_P + x] - B[x];
+  o[PR_ZA] = za;
+  o[PR_ZB] = zb;
+  for (int nn = 1; nn <= 14; ++nn) o[PR_NH + nn - 1] = 0.5 * nn * ig;
+  if (r == 0)
+    for (int x = 0; x < 3; ++x) ab[3 * p + x] = AB[x];
+}
+
+// One thread per (ket list entry q, primitive ic): zeta_c and c_c / zeta_c.
+__global__ void aux_precompute(DevBasis aux, const int32_t* __restrict__ auxs, long long naux, int Kc,
+                               double* __restrict__ rec, double* __restrict__ cxyz) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= naux * Kc) return;
+  long long q = i / Kc;
+  int ic = (int)(i - q * Kc);
+  int s = auxs[q];
+  double z = aux.exps[aux.off[s] + ic], c = aux.coefs[aux.off[s] + ic];
+  rec[i * kAuxRec + 0] = z;
+  rec[i * kAuxRec + 1] = c / z;
+  if (ic == 0)
+    for (int x = 0; x < 3; ++x) cxyz[3 * q + x] = aux.xyz[3 * s + x];
+}
+
+// ---------------------------------------------------------------------------
+// integral kernel
+// ---------------------------------------------------------------------------
+
+#define BUF_T(b, idx, t) ((b).base + (idx) * (b).si + (t) * (b).st)
+#define BUF_TG(b, idx, g, t) ((b).base + (idx) * (b).si + (g) * (b).sg + (t) * (b).st)
+
+// item w -> (t, x) for per-triple stages with X targets
+__device__ __forceinline__ void dec2(unsigned w, int mode, const FDiv& fT, const FDiv& fX, int& t, int& x) {
+  if (mode == 0) {
+    unsigned q = fT.div(w);
+    t = (int)(w - q * fT.d);
+    x = (int)q;
+  } else {
+    unsigned q = fX.div(w);
+    x = (int)(w - q * fX.d);
+    t = (int)q;
+  }
+}
+
+// item w -> (t, g, x) for per-(triple, primitive) stages
+__device__ __forceinline__ void dec3(unsigned w, int mode, const FDiv& fT, const FDiv& fG, const FDiv& fX, int& t,
+                                     int& g, int& x) {
+  if (mode == 0) {
+    unsigned q = fT.div(w);
+    t = (int)(w - q * fT.d);
+    unsigned r = fG.div(q);
+    g = (int)(q - r * fG.d);
+    x = (int)r;
+  } else {
+    unsigned q = fX.div(w);
+    x = (int)(w - q * fX.d);
+    unsigned r = fG.div(q);
+    g = (int)(q - r * fG.d);
+    t = (int)r;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__ ClassDesc d) {
+  extern __shared__ double sm[];
+  const unsigned tid = threadIdx.x;
+  const int T = d.T, G = d.G, mode = d.mode, lc = d.lc, Lab = d.Lab;
+  FDiv fT, fG, fKc;
+  fT.init(T);
+  fG.init(G);
+  fKc.init(d.Kc);
+  const int auxsz = 3 + kAuxRec * d.Kc;
+
+  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
+    const long long sub = tile / d.ntile_aux;
+    const int aux0 = (int)(tile - sub * d.ntile_aux) * T;
+    const int tv = (int)min((long long)T, d.naux - aux0);
+    const int4 sp = __ldg(d.subpairs + sub);
+    const long long pair = sp.x;
+    const int kab = sp.z, accum = sp.w;
+    const int K = kab * d.Kc;
+    const int nchunk = (K + G - 1) / G;
+    __syncthreads();  // previous tile done with shared memory
+    {
+      // this sub-pair's primitive-pair records, in its orientation
+      for (int i = tid; i < kab * kPairRec; i += kThreads) {
+        const int g = i / kPairRec, f = i - g * kPairRec;
+        int fs = f;
+        if (d.orient) {
+          if (f >= PR_PA && f < PR_PA + 3) fs = f + (PR_PB - PR_PA);
+          else if (f == PR_ZA) fs = PR_ZB;
+          else if (f == PR_ZB) fs = PR_ZA;
+        }
+        const long long r = pair * d.Kab_rec + __ldg(d.primidx + sp.y + g);
+        sm[d.pair_base + i] = d.pairrec[r * kPairRec + fs];
+      }
+      if (tid < 3) {
+        const double ab = d.pairab[pair * 3 + tid];
+        sm[d.ab_base + tid] = d.orient ? -ab : ab;
+      }
+      for (int i = tid; i < tv * auxsz; i += kThreads) {
+        int t = i / auxsz, r = i - t * auxsz;
+        sm[d.aux_base + i] = r < 3 ? d.auxc[(long long)(aux0 + t) * 3 + r]
+                                   : d.auxrec[(long long)(aux0 + t) * d.Kc * kAuxRec + (r - 3)];
+      }
+      FDiv fA;
+      fA.init(d.NACC);
+      for (unsigned w = tid; w < (unsigned)(T * d.NACC); w += kThreads) {
+        int t, a;
+        dec2(w, mode, fT, fA, t, a);
+        sm[BUF_T(d.P, a, t)] = 0.0;
+      }
+    }
+    __syncthreads();
+
+    for (int chunk = 0; chunk < nchunk; ++chunk) {
+      const int p0 = chunk * G;
+      const int gcnt = min(G, K - p0);
+      // ---- stage A: geometry, Boys function, [00|0]^(m) and recurrence factors
+      for (unsigned w = tid; w < (unsigned)(T * G); w += kThreads) {
+        int t, g;
+        if (mode == 0) {
+          unsigned q = fT.div(w);
+          t = (int)(w - q * T);
+          g = (int)q;
+        } else {
+          unsigned q = fG.div(w);
+          g = (int)(w - q * G);
+          t = (int)q;
+        }
+        if (t >= tv || g >= gcnt) continue;
+        const int p = p0 + g;
+        const int ip = (int)fKc.div(p), ic = p - ip * d.Kc;
+        const double* pr = sm + d.pair_base + ip * kPairRec;
+        const double* ax = sm + d.aux_base + t * auxsz;
+        const double gam = pr[PR_G], zc = ax[3 + kAuxRec * ic], ccp = ax[4 + kAuxRec * ic];
+        const double s = gam + zc;
+        const double rs = rsqrt_fp64(s);
+        const double r = rs * rs;
+        const double rg = zc * r;    // rho / gamma
+        const double gr = gam * r;   // rho / zeta_c
+        const double PCx = pr[PR_P] - ax[0], PCy = pr[PR_P + 1] - ax[1], PCz = pr[PR_P + 2] - ax[2];
+        const double pc2 = fma(PCz, PCz, fma(PCy, PCy, PCx * PCx));
+        const double rho = gam * rg;
+        const double Tb = rho * pc2;
+        const double pref = pr[PR_K] * ccp * rs;
+        const int fb = BUF_TG(d.F, 0, g, t);
+        const int fs = d.F.si;
+        sm[fb] = rg * PCx;
+        sm[fb + fs] = rg * PCy;
+        sm[fb + 2 * fs] = rg * PCz;
+        sm[fb + 3 * fs] = rg;
+        if (lc > 0) {
+          double X[3] = {gr * PCx, gr * PCy, gr * PCz};
+          for (int i = 0; i < 3; ++i) {
+            double v = X[i];
+            sm[fb + (4 + i * lc) * fs] = v;
+            for (int j = 2; j <= lc; ++j) {
+              v *= X[i];
+              sm[fb + (4 + i * lc + j - 1) * fs] = v;
+            }
+          }
+          double Y = 0.5 * r, v = Y;
+          sm[fb + (4 + 3 * lc) * fs] = v;
+          for (int k = 2; k <= lc; ++k) {
+            v *= Y;
+            sm[fb + (4 + 3 * lc + k - 1) * fs] = v;
+          }
+        }
+        boys_scaled(d.boys_tab, d.boys_mid, d.boys_cL, d.L, lc, Tb, pref, sm + BUF_TG(d.V, 0, g, t), d.V.si);
+      }
+      __syncthreads();
+      // ---- weights W_{k,n} = Y^k X^n (Eq. a0cv2)
+      {
+        FDiv fX;
+        fX.init(d.nW);
+        const unsigned n = (unsigned)(T * G * d.nW);
+        for (unsigned w = tid; w < n; w += kThreads) {
+          int t, g, x;
+          dec3(w, mode, fT, fG, fX, t, g, x);
+          if (t >= tv || g >= gcnt) continue;
+          const int4 it = __ldg(d.wtab + x);
+          const int dst = it.x & 0xFFFF, cnt = it.z >> 16;
+          const int fb = BUF_TG(d.F, 0, g, t), fs = d.F.si;
+          double v = 1.0;
+          if (cnt > 0) v = sm[fb + (it.x >> 16) * fs];
+          if (cnt > 1) v *= sm[fb + (it.y & 0xFFFF) * fs];
+          if (cnt > 2) v *= sm[fb + (it.y >> 16) * fs];
+          if (cnt > 3) v *= sm[fb + (it.z & 0xFFFF) * fs];
+          sm[BUF_TG(d.W, dst, g, t)] = v;
+        }
+      }
+      // ---- VRR1, level by level (Eq. vrr1)
+      for (int e = 1; e <= Lab; ++e) {
+        const int j0 = d.vlev_start[e - 1];
+        const int nl = d.vlev_start[e] - j0;
+        FDiv fX;
+        fX.init(nl);
+        const unsigned n = (unsigned)(T * G * nl);
+        for (unsigned w = tid; w < n; w += kThreads) {
+          int t, g, x;
+          dec3(w, mode, fT, fG, fX, t, g, x);
+          if (t >= tv || g >= gcnt) continue;
+          const uint4 it = __ldg(d.vtab + j0 + x);
+          const int dst = it.x & 0xFFFF, a = it.x >> 16, an = it.y & 0xFFFF, b = it.y >> 16, bn = it.z & 0xFFFF;
+          const int axis = (it.z >> 16) & 0xF, nq = (it.z >> 20) & 0xF;
+          const int p = p0 + g;
+          const int ip = (int)fKc.div(p);
+          const double* pr = sm + d.pair_base + ip * kPairRec;
+          const int vb = BUF_TG(d.V, 0, g, t), vs = d.V.si;
+          const int fb = BUF_TG(d.F, 0, g, t), fs = d.F.si;
+          double val = pr[PR_PA + axis] * sm[vb + a * vs];
+          val = fma(-sm[fb + axis * fs], sm[vb + an * vs], val);
+          if (nq) {
+            double u = fma(-sm[fb + 3 * fs], sm[vb + bn * vs], sm[vb + b * vs]);
+            val = fma(pr[PR_NH + nq - 1], u, val);
+          }
+          sm[vb + dst * vs] = val;
+        }
+        __syncthreads();
+      }
+      if (Lab == 0) __syncthreads();
+      // ---- accumulate CVRR2 prerequisites over the chunk's primitives
+      {
+        FDiv fX;
+        fX.init(d.NACC);
+        const unsigned n = (unsigned)(T * d.NACC);
+        for (unsigned w = tid; w < n; w += kThreads) {
+          int t, a;
+          dec2(w, mode, fT, fX, t, a);
+          if (t >= tv) continue;
+          const unsigned e = __ldg(d.atab + a);
+          const int vi = e & 0xFFFF, wi = e >> 16;
+          const int pa = BUF_T(d.P, a, t);
+          double acc = sm[pa];
+          int vb = BUF_TG(d.V, vi, 0, t), wb = BUF_TG(d.W, wi, 0, t);
+          for (int g = 0; g < gcnt; ++g) acc = fma(sm[vb + g * d.V.sg], sm[wb + g * d.W.sg], acc);
+          sm[pa] = acc;
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- CVRR2 targets (a 0|c) by the n-quantum gather (Sec. 2.5.4)
+    {
+      FDiv fX;
+      fX.init(d.ngt);
+      const unsigned n = (unsigned)(T * d.ngt);
+      for (unsigned w = tid; w < n; w += kThreads) {
+        int t, r;
+        dec2(w, mode, fT, fX, t, r);
+        if (t >= tv) continue;
+        const int id = __ldg(d.gdst + r);
+        const int q0 = __ldg(d.gptr + id), q1 = __ldg(d.gptr + id + 1);
+        double s = 0.0;
+        for (int q = q0; q < q1; ++q) {
+          const unsigned e = __ldg(d.gterm + q);
+          s = fma(__ldg(d.pal + (e >> 20)), sm[BUF_T(d.P, e & 0xFFFFF, t)], s);
+        }
+        sm[BUF_T(d.Gb, id, t)] = s;
+      }
+    }
+    __syncthreads();
+    // ---- ket: Cartesian -> solid harmonic
+    {
+      FDiv fX, fC;
+      const int nx = d.nkrow * d.nC;
+      fX.init(nx);
+      fC.init(d.nC);
+      const unsigned n = (unsigned)(T * nx);
+      for (unsigned w = tid; w < n; w += kThreads) {
+        int t, x;
+        dec2(w, mode, fT, fX, t, x);
+        if (t >= tv) continue;
+        const int row = (int)fC.div(x), C = x - row * d.nC;
+        const int q0 = __ldg(d.kptr + C), q1 = __ldg(d.kptr + C + 1);
+        double s = 0.0;
+        for (int q = q0; q < q1; ++q) {
+          const int2 e = __ldg(d.kent + q);
+          s = fma(__ldg(d.pal + e.y), sm[BUF_T(d.Gb, row * d.ncc + e.x, t)], s);
+        }
+        sm[BUF_T(d.H[0], x, t)] = s;
+      }
+    }
+    __syncthreads();
+    // ---- HRR (Eq. hrr), level by level
+    for (int j = 1; j <= d.lb; ++j) {
+      FDiv fX, fC;
+      const int nx = d.hrows[j] * d.nC;
+      fX.init(nx);
+      fC.init(d.nC);
+      const unsigned n = (unsigned)(T * nx);
+      const Buf hi = d.H[j - 1], ho = d.H[j];
+      for (unsigned w = tid; w < n; w += kThreads) {
+        int t, x;
+        dec2(w, mode, fT, fX, t, x);
+        if (t >= tv) continue;
+        const int r = (int)fC.div(x), C = x - r * d.nC;
+        const int4 e = __ldg(d.htab + d.hstart[j] + r);
+        const double v = fma(sm[d.ab_base + e.w], sm[BUF_T(hi, e.z * d.nC + C, t)], sm[BUF_T(hi, e.y * d.nC + C, t)]);
+        sm[BUF_T(ho, e.x * d.nC + C, t)] = v;
+      }
+      __syncthreads();
+    }
+    // ---- optional solid-harmonic bra
+    Buf cur = d.H[d.lb];
+    if (d.nbA) {
+      FDiv fX, fC, fB;
+      const int nx = d.nbA * d.nC;
+      fX.init(nx);
+      fC.init(d.nC);
+      fB.init(d.ncB);
+      const unsigned n = (unsigned)(T * nx);
+      for (unsigned w = tid; w < n; w += kThreads) {
+        int t, x;
+        dec2(w, mode, fT, fX, t, x);
+        if (t >= tv) continue;
+        const int row = (int)fC.div(x), C = x - row * d.nC;
+        const int A = (int)fB.div(row), ib = row - A * d.ncB;
+        const int q0 = __ldg(d.baptr + A), q1 = __ldg(d.baptr + A + 1);
+        double s;
+        const int2 e0 = __ldg(d.baent + q0);
+        if (q1 - q0 == 1 && e0.y == 0) {
+          s = sm[BUF_T(cur, (e0.x * d.ncB + ib) * d.nC + C, t)];
+        } else {
+          s = 0.0;
+          for (int q = q0; q < q1; ++q) {
+            const int2 e = __ldg(d.baent + q);
+            s = fma(__ldg(d.pal + e.y), sm[BUF_T(cur, (e.x * d.ncB + ib) * d.nC + C, t)], s);
+          }
+        }
+        sm[BUF_T(d.BA, x, t)] = s;
+      }
+      __syncthreads();
+      cur = d.BA;
+    }
+    if (d.nbB) {
+      FDiv fX, fC, fB;
+      const int nx = d.nbB * d.nC;
+      const int nBs = d.nB;
+      fX.init(nx);
+      fC.init(d.nC);
+      fB.init(nBs);
+      const unsigned n = (unsigned)(T * nx);
+      for (unsigned w = tid; w < n; w += kThreads) {
+        int t, x;
+        dec2(w, mode, fT, fX, t, x);
+        if (t >= tv) continue;
+        const int row = (int)fC.div(x), C = x - row * d.nC;
+        const int A = (int)fB.div(row), B = row - A * nBs;
+        const int q0 = __ldg(d.bbptr + B), q1 = __ldg(d.bbptr + B + 1);
+        double s;
+        const int2 e0 = __ldg(d.bbent + q0);
+        if (q1 - q0 == 1 && e0.y == 0) {
+          s = sm[BUF_T(cur, (A * d.ncB + e0.x) * d.nC + C, t)];
+        } else {
+          s = 0.0;
+          for (int q = q0; q < q1; ++q) {
+            const int2 e = __ldg(d.bbent + q);
+            s = fma(__ldg(d.pal + e.y), sm[BUF_T(cur, (A * d.ncB + e.x) * d.nC + C, t)], s);
+          }
+        }
+        sm[BUF_T(d.BB, x, t)] = s;
+      }
+      __syncthreads();
+      cur = d.BB;
+    }
+    // ---- store the tile's contiguous output block (transposed into the
+    // caller's (A, B) order for B-oriented sub-pairs; added to the block
+    // already written by the A-oriented launch when the pair has both)
+    {
+      FDiv fB, fBC, fC;
+      fB.init(d.nblk);
+      fBC.init(d.onB * d.nC);
+      fC.init(d.nC);
+      double* o = d.out + (pair * d.naux + aux0) * (long long)d.nblk;
+      const unsigned n = (unsigned)(tv * d.nblk);
+      for (unsigned w = tid; w < n; w += kThreads) {
+        const unsigned t = fB.div(w);
+        const int idx = (int)(w - t * d.nblk);
+        int sidx = idx;
+        if (d.orient) {
+          const int A = (int)fBC.div(idx), rem = idx - A * d.onB * d.nC;
+          const int B = (int)fC.div(rem), C = rem - B * d.nC;
+          sidx = (B * d.onA + A) * d.nC + C;
+        }
+        double v = sm[BUF_T(cur, sidx, (int)t)];
+        if (accum) v += o[w];
+        o[w] = v;
+      }
+    }
+  }
+}
+
+// Boys function evaluation for lx3c_boys: out[i*(mmax+1)+m] = F_m(T[i]).
+__global__ void boys_kernel(const double* __restrict__ Tv, long long n, int mmax, const double* __restrict__ tab,
+                            const double* __restrict__ mid, double cL, double* __restrict__ out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  boys_scaled(tab, mid, cL, mmax, 0, Tv[i], 1.0, out + i * (mmax + 1), 1);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers (called from capi.cu)
+// ---------------------------------------------------------------------------
+
+cudaError_t init_constants() {
+  double v[32];
+  for (int m = 0; m < 32; ++m) v[m] = 1.0 / (2 * m + 1);
+  return cudaMemcpyToSymbol(c_inv2m1, v, sizeof(v));
+}
+
+cudaError_t launch_pair_precompute(const DevBasis& orb, const int32_t* pairs, long long npair, int Ka, int Kb,
+                                   double* rec, double* ab, cudaStream_t st) {
+  long long n = npair * Ka * Kb;
+  if (n == 0) return cudaSuccess;
+  pair_precompute<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(orb, pairs, npair, Ka, Kb, rec, ab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aux_precompute(const DevBasis& aux, const int32_t* auxs, long long naux, int Kc, double* rec,
+                                  double* cxyz, cudaStream_t st) {
+  long long n = naux * Kc;
+  if (n == 0) return cudaSuccess;
+  aux_precompute<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(aux, auxs, naux, Kc, rec, cxyz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(eri3c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  eri3c_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boys(const double* T, long long n, int mmax, const double* tab, const double* mid, double cL,
+                        double* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  boys_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(T, n, mmax, tab, mid, cL, out);
+  return cudaGetLastError();
+}
+
+int eri3c_occupancy(int smem_bytes) {
+  int nb = 0;
+  cudaFuncSetAttribute(eri3c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eri3c_kernel, kThreads, smem_bytes) != cudaSuccess) return 1;
+  return nb < 1 ? 1 : nb;
+}
+
+}  // namespace lx3c

@@ -1,0 +1,153 @@
+// Internal types shared by the host planner (plan.cu) and the device kernels
+// (eri3c.cu).  Not part of the public C ABI.
+#pragma once
+#include <cstdint>
+#include <vector_types.h>
+#include <vector>
+#include <string>
+
+namespace lx3c {
+
+constexpr int kThreads = 256;            // threads per CTA of the integral kernels
+constexpr int kMaxLev = 16;              // VRR1 levels (la+lb) and HRR levels (lb)
+constexpr int kPairRec = 28;             // doubles per primitive-pair record
+constexpr int kPairNHalf = 13;           // offset of n/(2 gamma), n = 1..14
+constexpr int kAuxRec = 2;               // doubles per ket primitive record: zeta_c, c_c/zeta_c
+constexpr int kBoysMmax = 24;            // Boys table covers F_0..F_24
+constexpr int kBoysNF = kBoysMmax + 2;   // functions per interval: F_0..F_24, exp(-T)
+constexpr int kBoysPerUnit = 8;          // intervals per unit of T (width 1/8)
+constexpr int kBoysNInt = 117 * kBoysPerUnit;
+constexpr double kBoysTMax = 117.0;
+constexpr int kBoysDeg = 7;              // degree of the interpolating polynomial (Sec. 2.5.2)
+
+// Pair record fields (doubles), one record per primitive pair (a_i, b_j):
+//   0 gamma = za+zb
+//   1 Kab'  = c_a c_b exp(-za zb/gamma |AB|^2) * 2 pi^{5/2} / gamma
+//   2..4 P, 5..7 PA = P - A, 8..10 PB = P - B, 11 za, 12 zb,
+//   13+n-1 = n/(2 gamma) for n = 1..14
+// In shared memory a tile's records are stored in its orientation: for a
+// sub-pair whose recurrences run on centre B the PB and zb fields are copied
+// into the PA and za slots.
+enum PairField { PR_G = 0, PR_K = 1, PR_P = 2, PR_PA = 5, PR_PB = 8, PR_ZA = 11, PR_ZB = 12, PR_NH = kPairNHalf };
+
+// A shared-memory buffer: element (idx, g, t) lives at base + idx*si + g*sg + t*st
+// (in doubles).  Per-triple buffers have sg = 0.
+struct Buf {
+  int base, si, sg, st;
+};
+
+// Everything a class kernel launch needs.  Passed by value (__grid_constant__).
+struct ClassDesc {
+  // class
+  int la, lb, lc, Lab, L, bra_pure;
+  int ncA, ncB, ncc;       // Cartesian sizes of the bra shells and the ket
+  int nA, nB, nC, nblk;    // output block dims (nC = 2lc+1), nblk = nA*nB*nC
+  int Kab, Kc, K, G, nchunk;  // Kab, K: largest sub-pair's primitive pairs, times Kc
+  int Kab_rec;             // primitive-pair records per pair in pairrec (Ka*Kb)
+  // orientation: 0 recurrences on A (class (la,lb)); 1 on B (class (lb,la)),
+  // the block is then stored transposed into the (A, B) layout of the pair list
+  int orient;
+  int onA, onB;            // output block dims of the caller's (la, lb) order
+  long long nsub;          // sub-pairs in this launch
+  const int4* subpairs;    // {pair index, first entry in primidx, count, accumulate flag}
+  const int* primidx;      // primitive-pair indices (ia*Kb + ib) of each sub-pair
+  // tiling: a tile is (one sub-pair, T consecutive ket shells of the list)
+  int T, Tp, mode;         // mode 0: triple index fastest across lanes; 1: target index fastest
+  int ntile_aux;
+  long long ntiles, npair, naux;
+  // per-slot sizes
+  int NV, NW, NF, NACC;
+  // VRR1 levels e = 1..Lab: items [vlev_start[e-1], vlev_start[e])
+  int vlev_start[kMaxLev + 1];
+  int nW;                  // weight items (= NW)
+  int ngt;                 // gather targets
+  int nkrow;               // rows (bra Cartesian functions) entering the ket transform
+  int hrows[kMaxLev + 1];  // rows per HRR level (level 0 = nkrow)
+  int hstart[kMaxLev + 1]; // first htab entry of level j (j >= 1)
+  int nbA, nbB;            // bra transform output rows (A,b) and (A,B), 0 if none
+  // tables (device)
+  const uint4* vtab;       // VRR1 items
+  const int4* wtab;        // weight items: F-buffer sources and count
+  const unsigned* atab;    // accumulator -> vidx | widx<<16
+  const int* gptr;         // gather CSR row pointers (by target id)
+  const unsigned* gterm;   // gather terms: pidx | coef_id<<20
+  const int* gdst;         // gather item r -> target id (items sorted by term count)
+  const double* pal;       // coefficient palette
+  const int* kptr;         // ket CSR by C
+  const int2* kent;        // (c, coef_id)
+  const int4* htab;        // HRR rows: dst_row, hi_row, lo_row, axis
+  const int* baptr;        // bra A transform CSR by A: entries (a, coef_id)
+  const int2* baent;
+  const int* bbptr;        // bra B transform CSR by B
+  const int2* bbent;
+  // shared-memory layout (doubles)
+  int pair_base, aux_base, ab_base;
+  Buf V, W, F, P, Gb, H[kMaxLev + 1], BA, BB, OUT;
+  int smem_doubles;
+  // data
+  const double* pairrec;   // [npair][Kab][kPairRec]
+  const double* pairab;    // [npair][3]  AB = A - B
+  const double* auxrec;    // [naux][Kc][kAuxRec]
+  const double* auxc;      // [naux][3]
+  const double* boys_tab;  // [kBoysNInt][kBoysNF][8]
+  const double* boys_mid;  // [kBoysNInt]
+  double boys_cL;          // Gamma(L+1/2)/2 for the large-T branch
+  double* out;
+};
+
+// Device view of a basis (shell tables in HBM).
+struct DevBasis {
+  const int32_t* l;
+  const int32_t* k;
+  const int64_t* off;
+  const double* xyz;
+  const double* exps;
+  const double* coefs;
+};
+
+// Host-side class tables (independent of the launch shape).
+struct ClassTables {
+  int la, lb, lc, bra_pure;
+  int NV, NW, NF, NACC;
+  std::vector<int> vlev_start;
+  std::vector<uint4> vtab;
+  std::vector<int4> wtab;
+  std::vector<unsigned> atab;
+  std::vector<int> gptr, gdst;
+  std::vector<unsigned> gterm;
+  std::vector<double> pal;
+  std::vector<int> kptr;
+  std::vector<int2> kent;
+  int nkrow;
+  std::vector<int> hrows, hstart;
+  std::vector<int4> htab;
+  std::vector<int> baptr, bbptr;
+  std::vector<int2> baent, bbent;
+  int nbA, nbB;
+  int nA, nB, nC, ncA, ncB, ncc;
+  // algorithmic FP64 flop counts (FMA = 2)
+  double flops_prim;      // per primitive triple
+  double flops_contr;     // per contracted triple (after the primitive loop)
+  // debug: (e comp, k, n comp) of each accumulator
+  std::vector<int4> acc_key;
+};
+
+// planner entry points (plan.cu)
+const ClassTables& class_tables(int la, int lb, int lc, int bra_pure);
+std::vector<double> solid_matrix(int l);   // [(m+l)*ncart(l) + c]
+int ncart(int l);
+int cart_index(int x, int y, int z);       // index of (x,y,z) within its shell
+// Boys tables (boys.cu)
+void boys_tables(std::vector<double>& tab, std::vector<double>& mid);
+long double boys_ref(int m, long double T);
+double boys_large_const(int L);
+
+// Launch-shape choice and descriptor fill (plan.cu)
+struct LaunchShape {
+  int T, G, mode;
+  int smem_bytes;
+};
+LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit);
+void fill_layout(ClassDesc& d, const ClassTables& ct, const LaunchShape& s);
+
+}  // namespace lx3c

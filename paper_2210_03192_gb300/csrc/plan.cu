@@ -1,0 +1,514 @@
+// Host-side class planner: builds, once per (la, lb | lc, bra_pure), the index
+// tables that drive the integral kernel's stages, and chooses the launch shape.
+//
+// Stages and the passages they follow (arXiv:2210.03192):
+//   [00|0]^(m)       Sec. 2.5.2 (Boys function times the prefactor)
+//   VRR1             Eq. vrr1: [a+1_i 0|0]^(m) = PA_i [a]^(m) - rho/gamma PC_i [a]^(m+1)
+//                              + a_i/(2 gamma) ([a-1_i]^(m) - rho/gamma [a-1_i]^(m+1))
+//   CVRR2 prerequisites  Eq. a0cv2: (e 0)_{k,n} = sum_prim Y^k X^n [e 0|0]^(lc),
+//                    Y = rho/(2 gamma zeta_c) = 1/(2(gamma+zeta_c)), X = rho/zeta_c PC
+//   CVRR2 targets    n-q form of Eq. cVRR2 (the printed closed form is garbled; the
+//                    reading used is sum over u <= min(a,c) of
+//                    prod_i C(a_i,u_i) C(c_i,u_i) u_i! (a-u 0)_{|u|, c-u})
+//   ket transform    Sec. 2.5.1 (Cartesian ket to solid harmonic)
+//   HRR              Eq. hrr: (a b+1_i|C) = (a+1_i b|C) + AB_i (a b|C)
+//   bra transform    optional (solid-harmonic bra)
+#include <vector_types.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <set>
+#include <stdexcept>
+#include <tuple>
+
+#include "lx3c_internal.h"
+
+namespace lx3c {
+
+int ncart(int l) { return l < 0 ? 0 : (l + 1) * (l + 2) / 2; }
+
+int cart_index(int x, int y, int z) {
+  int l = x + y + z, idx = 0;
+  for (int ax = l; ax > x; --ax) idx += l - ax + 1;
+  return idx + (l - x) - y;
+}
+
+namespace {
+
+struct C3 {
+  int v[3];
+  int l() const { return v[0] + v[1] + v[2]; }
+  bool operator<(const C3& o) const { return std::tie(v[0], v[1], v[2]) < std::tie(o.v[0], o.v[1], o.v[2]); }
+  bool operator==(const C3& o) const { return v[0] == o.v[0] && v[1] == o.v[1] && v[2] == o.v[2]; }
+};
+
+std::vector<C3> cart(int l) {
+  std::vector<C3> out;
+  for (int x = l; x >= 0; --x)
+    for (int y = l - x; y >= 0; --y) out.push_back(C3{{x, y, l - x - y}});
+  return out;
+}
+
+double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return std::round(r);
+}
+
+double fact(int n) {
+  double r = 1.0;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+
+}  // namespace
+
+// Real solid harmonics, Racah normalisation, m = -l..l, by the closed
+// expansion of S_lm in Cartesian monomials (standard Schlegel-Frisch /
+// Helgaker form): S_lm = N_lm sum_{t,u,v} C_tuv x^{2t+|m|-2(u+v)} y^{2(u+v)} z^{l-2t-|m|}.
+std::vector<double> solid_matrix(int l) {
+  int nc = ncart(l);
+  std::vector<double> T((2 * l + 1) * nc, 0.0);
+  for (int m = -l; m <= l; ++m) {
+    int am = m < 0 ? -m : m;
+    int vm2 = m < 0 ? 1 : 0;  // 2*v_m
+    long double N = 1.0L / (std::pow(2.0L, am) * (long double)fact(l)) *
+                    std::sqrt(2.0L * (long double)fact(l + am) * (long double)fact(l - am) / (m == 0 ? 2.0L : 1.0L));
+    for (int t = 0; t <= (l - am) / 2; ++t)
+      for (int u = 0; u <= t; ++u)
+        for (int vv = vm2; vv <= am; vv += 2) {  // vv = 2v
+          int sgn_exp = t + (vv - vm2) / 2;
+          long double c = ((sgn_exp & 1) ? -1.0L : 1.0L) * std::pow(0.25L, t) * binom(l, t) * binom(l - t, am + t) *
+                          binom(t, u) * binom(am, vv);
+          int ex = 2 * t + am - 2 * u - vv, ey = 2 * u + vv, ez = l - 2 * t - am;
+          if (ex < 0) continue;
+          T[(m + l) * nc + cart_index(ex, ey, ez)] += (double)(N * c);
+        }
+  }
+  return T;
+}
+
+namespace {
+
+unsigned pal_id(std::vector<double>& pal, std::map<double, int>& ids, double v) {
+  auto it = ids.find(v);
+  if (it != ids.end()) return it->second;
+  int id = (int)pal.size();
+  pal.push_back(v);
+  ids[v] = id;
+  return id;
+}
+
+ClassTables build(int la, int lb, int lc, int bra_pure) {
+  ClassTables ct;
+  ct.la = la; ct.lb = lb; ct.lc = lc; ct.bra_pure = bra_pure;
+  const int Lab = la + lb;
+  ct.ncA = ncart(la); ct.ncB = ncart(lb); ct.ncc = ncart(lc);
+  ct.nC = 2 * lc + 1;
+  ct.nA = bra_pure ? 2 * la + 1 : ct.ncA;
+  ct.nB = bra_pure ? 2 * lb + 1 : ct.ncB;
+  std::map<double, int> palids;
+  pal_id(ct.pal, palids, 1.0);  // id 0 is always 1.0
+
+  // ---------------- HRR dependency analysis (Eq. hrr) ----------------
+  // nodes (a, b) per level j = |b|; level lb: |a| = la, all (a, b)
+  std::vector<std::vector<std::pair<C3, C3>>> lev(lb + 1);
+  std::vector<std::map<std::pair<C3, C3>, int>> levidx(lb + 1);
+  std::vector<std::map<C3, int>> baxis(lb + 1);
+  for (auto& a : cart(la))
+    for (auto& b : cart(lb)) {
+      levidx[lb][{a, b}] = (int)lev[lb].size();
+      lev[lb].push_back({a, b});
+    }
+  for (int j = lb; j >= 1; --j) {
+    // choose, for every b on level j, the axis to lower: greedy cover of the
+    // needed b's by as few predecessors b-1_i as possible
+    std::set<C3> need;
+    for (auto& n : lev[j]) need.insert(n.second);
+    while (!need.empty()) {
+      C3 best{{0, 0, 0}};
+      int bestcount = -1;
+      for (auto& bp : cart(j - 1)) {
+        int cnt = 0;
+        for (int i = 0; i < 3; ++i) {
+          C3 b = bp;
+          b.v[i]++;
+          if (need.count(b)) ++cnt;
+        }
+        if (cnt > bestcount) { bestcount = cnt; best = bp; }
+      }
+      for (int i = 0; i < 3; ++i) {
+        C3 b = best;
+        b.v[i]++;
+        if (need.count(b)) { baxis[j][b] = i; need.erase(b); }
+      }
+    }
+    std::set<std::pair<C3, C3>> prev;
+    for (auto& n : lev[j]) {
+      int i = baxis[j][n.second];
+      C3 a1 = n.first, bm = n.second;
+      a1.v[i]++;
+      bm.v[i]--;
+      prev.insert({a1, bm});
+      prev.insert({n.first, bm});
+    }
+    // order level j-1 nodes: by |a|, then a, then b
+    std::vector<std::pair<C3, C3>> pv(prev.begin(), prev.end());
+    std::sort(pv.begin(), pv.end(), [](const std::pair<C3, C3>& x, const std::pair<C3, C3>& y) {
+      if (x.first.l() != y.first.l()) return x.first.l() < y.first.l();
+      int ix = cart_index(x.first.v[0], x.first.v[1], x.first.v[2]);
+      int iy = cart_index(y.first.v[0], y.first.v[1], y.first.v[2]);
+      if (ix != iy) return ix < iy;
+      return cart_index(x.second.v[0], x.second.v[1], x.second.v[2]) <
+             cart_index(y.second.v[0], y.second.v[1], y.second.v[2]);
+    });
+    lev[j - 1] = pv;
+    for (size_t r = 0; r < pv.size(); ++r) levidx[j - 1][pv[r]] = (int)r;
+  }
+  // e0 rows (level 0): needed bra functions (a, 0)
+  std::vector<C3> erows;
+  for (auto& n : lev[0]) erows.push_back(n.first);
+  ct.nkrow = (int)erows.size();
+  ct.hrows.assign(lb + 1, 0);
+  ct.hstart.assign(lb + 2, 0);
+  ct.hrows[0] = ct.nkrow;
+  for (int j = 1; j <= lb; ++j) {
+    ct.hstart[j] = (int)ct.htab.size();
+    ct.hrows[j] = (int)lev[j].size();
+    for (size_t r = 0; r < lev[j].size(); ++r) {
+      auto& n = lev[j][r];
+      int i = baxis[j][n.second];
+      C3 a1 = n.first, bm = n.second;
+      a1.v[i]++;
+      bm.v[i]--;
+      ct.htab.push_back(int4{(int)r, levidx[j - 1].at({a1, bm}), levidx[j - 1].at({n.first, bm}), i});
+    }
+  }
+  ct.hstart[lb + 1] = (int)ct.htab.size();
+
+  // ---------------- VRR1 buffer and items (Eq. vrr1) ----------------
+  std::vector<int> voff(Lab + 2, 0);
+  for (int e = 0; e <= Lab; ++e) voff[e + 1] = voff[e] + ncart(e) * (Lab - e + 1);
+  ct.NV = voff[Lab + 1];
+  auto vidx = [&](int e, int m, const C3& c) { return voff[e] + (m - lc) * ncart(e) + cart_index(c.v[0], c.v[1], c.v[2]); };
+  ct.vlev_start.assign(Lab + 1, 0);
+  for (int e = 1; e <= Lab; ++e) {
+    ct.vlev_start[e - 1] = (int)ct.vtab.size();
+    std::vector<uint4> simple, full;
+    for (auto& t : cart(e)) {
+      int ax = -1;
+      for (int i = 0; i < 3; ++i)
+        if (t.v[i] == 1) { ax = i; break; }
+      if (ax < 0)
+        for (int i = 0; i < 3; ++i)
+          if (t.v[i] > 0 && (ax < 0 || t.v[i] > t.v[ax])) ax = i;
+      int n = t.v[ax] - 1;
+      C3 s1 = t;
+      s1.v[ax]--;
+      C3 s2 = s1;
+      if (n > 0) s2.v[ax]--;
+      for (int m = lc; m <= lc + Lab - e; ++m) {
+        unsigned dst = vidx(e, m, t), a = vidx(e - 1, m, s1), an = vidx(e - 1, m + 1, s1);
+        unsigned b = n > 0 ? vidx(e - 2, m, s2) : 0u, bn = n > 0 ? vidx(e - 2, m + 1, s2) : 0u;
+        uint4 it{dst | (a << 16), an | (b << 16), bn | ((unsigned)ax << 16) | ((unsigned)n << 20), 0u};
+        (n > 0 ? full : simple).push_back(it);
+      }
+    }
+    ct.vtab.insert(ct.vtab.end(), simple.begin(), simple.end());
+    ct.vtab.insert(ct.vtab.end(), full.begin(), full.end());
+  }
+  ct.vlev_start[Lab] = (int)ct.vtab.size();
+
+  // ---------------- weights W_{k,n} = Y^k X^n (Eq. a0cv2) ----------------
+  // F buffer: 0..2 (rho/gamma) PC, 3 rho/gamma, 4 + i*lc + (j-1) X_i^j, 4 + 3lc + (k-1) Y^k
+  ct.NF = 4 + 4 * lc;
+  std::vector<int> woff(lc + 2, 0);
+  for (int k = 0; k <= lc; ++k) woff[k + 1] = woff[k] + ncart(lc - k);
+  ct.NW = woff[lc + 1];
+  {
+    std::vector<std::pair<int, int4>> items;
+    for (int k = 0; k <= lc; ++k)
+      for (auto& n : cart(lc - k)) {
+        int w = woff[k] + cart_index(n.v[0], n.v[1], n.v[2]);
+        std::vector<int> src;
+        if (k > 0) src.push_back(4 + 3 * lc + (k - 1));
+        for (int i = 0; i < 3; ++i)
+          if (n.v[i] > 0) src.push_back(4 + i * lc + (n.v[i] - 1));
+        while (src.size() < 4) src.push_back(0xFFFF);
+        int cnt = 0;
+        for (int s : src) cnt += s != 0xFFFF;
+        int4 it{w | (src[0] << 16), src[1] | (src[2] << 16), src[3] | (cnt << 16), 0};
+        items.push_back({cnt, it});
+      }
+    std::stable_sort(items.begin(), items.end(), [](auto& x, auto& y) { return x.first < y.first; });
+    for (auto& it : items) ct.wtab.push_back(it.second);
+  }
+
+  // ---------------- CVRR2 targets and prerequisites (Sec. 2.5.4) ----------------
+  std::map<std::tuple<C3, int, C3>, int> accmap;
+  std::vector<std::tuple<C3, int, C3>> acckeys;
+  auto cl = cart(lc);
+  struct Tgt { int id; std::vector<unsigned> terms; };
+  std::vector<Tgt> tg;
+  std::vector<std::vector<std::pair<std::tuple<C3, int, C3>, double>>> rawterms;
+  for (int r = 0; r < ct.nkrow; ++r) {
+    const C3& a = erows[r];
+    for (size_t ic = 0; ic < cl.size(); ++ic) {
+      const C3& c = cl[ic];
+      std::vector<std::pair<std::tuple<C3, int, C3>, double>> terms;
+      for (int ux = 0; ux <= std::min(a.v[0], c.v[0]); ++ux)
+        for (int uy = 0; uy <= std::min(a.v[1], c.v[1]); ++uy)
+          for (int uz = 0; uz <= std::min(a.v[2], c.v[2]); ++uz) {
+            int u[3] = {ux, uy, uz};
+            double coef = 1.0;
+            C3 e, n;
+            for (int i = 0; i < 3; ++i) {
+              coef *= binom(a.v[i], u[i]) * binom(c.v[i], u[i]) * fact(u[i]);
+              e.v[i] = a.v[i] - u[i];
+              n.v[i] = c.v[i] - u[i];
+            }
+            terms.push_back({std::make_tuple(e, ux + uy + uz, n), coef});
+          }
+      rawterms.push_back(terms);
+      for (auto& t : terms)
+        if (!accmap.count(t.first)) { accmap[t.first] = 0; }
+    }
+  }
+  // accumulator order: by |e|, e, k, n
+  for (auto& kv : accmap) acckeys.push_back(kv.first);
+  std::sort(acckeys.begin(), acckeys.end(), [](auto& x, auto& y) {
+    const C3 &ex = std::get<0>(x), &ey = std::get<0>(y);
+    if (ex.l() != ey.l()) return ex.l() < ey.l();
+    int ix = cart_index(ex.v[0], ex.v[1], ex.v[2]), iy = cart_index(ey.v[0], ey.v[1], ey.v[2]);
+    if (ix != iy) return ix < iy;
+    if (std::get<1>(x) != std::get<1>(y)) return std::get<1>(x) < std::get<1>(y);
+    const C3 &nx = std::get<2>(x), &ny = std::get<2>(y);
+    return cart_index(nx.v[0], nx.v[1], nx.v[2]) < cart_index(ny.v[0], ny.v[1], ny.v[2]);
+  });
+  for (size_t i = 0; i < acckeys.size(); ++i) accmap[acckeys[i]] = (int)i;
+  ct.NACC = (int)acckeys.size();
+  for (auto& key : acckeys) {
+    const C3& e = std::get<0>(key);
+    int k = std::get<1>(key);
+    const C3& n = std::get<2>(key);
+    unsigned v = vidx(e.l(), lc, e);
+    unsigned w = woff[k] + cart_index(n.v[0], n.v[1], n.v[2]);
+    ct.atab.push_back(v | (w << 16));
+    ct.acc_key.push_back(int4{cart_index(e.v[0], e.v[1], e.v[2]) | (e.l() << 16), k,
+                              cart_index(n.v[0], n.v[1], n.v[2]) | ((lc - k) << 16), 0});
+  }
+  // gather CSR by target id = row*ncc + c, items sorted by descending term count
+  int ngt = ct.nkrow * ct.ncc;
+  ct.gptr.assign(ngt + 1, 0);
+  for (int id = 0; id < ngt; ++id) {
+    for (auto& t : rawterms[id]) {
+      unsigned pid = (unsigned)accmap[t.first];
+      unsigned cid = pal_id(ct.pal, palids, t.second);
+      ct.gterm.push_back(pid | (cid << 20));
+    }
+    ct.gptr[id + 1] = (int)ct.gterm.size();
+  }
+  ct.gdst.resize(ngt);
+  for (int i = 0; i < ngt; ++i) ct.gdst[i] = i;
+  std::stable_sort(ct.gdst.begin(), ct.gdst.end(), [&](int x, int y) {
+    return (ct.gptr[x + 1] - ct.gptr[x]) > (ct.gptr[y + 1] - ct.gptr[y]);
+  });
+
+  // ---------------- ket transform ----------------
+  auto Tc = solid_matrix(lc);
+  ct.kptr.assign(ct.nC + 1, 0);
+  for (int C = 0; C < ct.nC; ++C) {
+    for (int c = 0; c < ct.ncc; ++c) {
+      double v = Tc[C * ct.ncc + c];
+      if (v != 0.0) ct.kent.push_back(int2{c, (int)pal_id(ct.pal, palids, v)});
+    }
+    ct.kptr[C + 1] = (int)ct.kent.size();
+  }
+
+  // ---------------- bra transforms ----------------
+  ct.nbA = ct.nbB = 0;
+  if (bra_pure && la > 0) {
+    auto Ta = solid_matrix(la);
+    ct.baptr.assign(2 * la + 2, 0);
+    for (int A = 0; A < 2 * la + 1; ++A) {
+      for (int a = 0; a < ct.ncA; ++a) {
+        double v = Ta[A * ct.ncA + a];
+        if (v != 0.0) ct.baent.push_back(int2{a, (int)pal_id(ct.pal, palids, v)});
+      }
+      ct.baptr[A + 1] = (int)ct.baent.size();
+    }
+    ct.nbA = (2 * la + 1) * ct.ncB;
+  }
+  if (bra_pure && lb > 0) {
+    auto Tb = solid_matrix(lb);
+    ct.bbptr.assign(2 * lb + 2, 0);
+    for (int B = 0; B < 2 * lb + 1; ++B) {
+      for (int b = 0; b < ct.ncB; ++b) {
+        double v = Tb[B * ct.ncB + b];
+        if (v != 0.0) ct.bbent.push_back(int2{b, (int)pal_id(ct.pal, palids, v)});
+      }
+      ct.bbptr[B + 1] = (int)ct.bbent.size();
+    }
+    ct.nbB = ct.nA * (2 * lb + 1);
+  }
+  if (ct.pal.size() >= 4096) throw std::runtime_error("coefficient palette overflow");
+  if (ct.NACC >= (1 << 20) || ct.NV >= 65536 || ct.NW >= 65536) throw std::runtime_error("class too large");
+
+  // ---------------- algorithmic flop counts (FMA = 2) ----------------
+  double fp = 0;
+  fp += 32 + (lc > 0 ? 4.0 * (lc - 1) : 0.0);       // geometry, rsqrt, prefactor, factor powers
+  fp += 32 + 3.0 * Lab;                             // Boys (two degree-7 polynomials) and [00|0]^(m)
+  for (int e = 1; e <= Lab; ++e)
+    for (int i = ct.vlev_start[e - 1]; i < ct.vlev_start[e]; ++i) fp += ((ct.vtab[i].z >> 20) & 0xF) ? 7 : 3;
+  for (auto& w : ct.wtab) {
+    int cnt = (w.z >> 16) & 0xFFFF;
+    fp += cnt > 1 ? cnt - 1 : 0;
+  }
+  fp += 2.0 * ct.NACC;
+  ct.flops_prim = fp;
+  double fc = 2.0 * ct.gterm.size();
+  fc += 2.0 * ct.kent.size() * ct.nkrow;
+  for (int j = 1; j <= lb; ++j) fc += 2.0 * ct.hrows[j] * ct.nC;
+  auto bra = [&](const std::vector<int>& ptr, const std::vector<int2>& ent, int nother) {
+    double f = 0;
+    for (size_t A = 0; A + 1 < ptr.size(); ++A) {
+      int n = ptr[A + 1] - ptr[A];
+      bool copy = (n == 1 && ct.pal[ent[ptr[A]].y] == 1.0);
+      if (!copy) f += 2.0 * n;
+    }
+    return f * nother * ct.nC;
+  };
+  if (ct.nbA) fc += bra(ct.baptr, ct.baent, ct.ncB);
+  if (ct.nbB) fc += bra(ct.bbptr, ct.bbent, ct.nA);
+  ct.flops_contr = fc;
+  return ct;
+}
+
+}  // namespace
+
+const ClassTables& class_tables(int la, int lb, int lc, int bra_pure) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, ClassTables> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(la, lb, lc, bra_pure ? 1 : 0);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  return cache.emplace(key, build(la, lb, lc, bra_pure ? 1 : 0)).first->second;
+}
+
+// ---------------------------------------------------------------------------
+// Launch shape
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Sizes {
+  long long loop, P, Y, X, pair, aux, total;
+};
+
+// per-slot sizes (in doubles) of every stage buffer for a given T, G
+void buffer_sizes(const ClassTables& ct, int Kab, int Kc, int T, int G, int mode, Sizes& s,
+                  ClassDesc* d) {
+  int Tp = (mode == 0 && T > 1) ? (T | 1) : T;
+  if (mode == 0 && T > 1 && (T % 2 == 0)) Tp = T + 1;
+  auto per_t = [&](int n) -> long long { return mode == 0 ? (long long)n * Tp : (long long)T * n; };
+  auto per_tg = [&](int n) -> long long { return mode == 0 ? (long long)n * G * Tp : (long long)T * G * n; };
+  long long nK = (long long)ct.nkrow * ct.nC, nG = (long long)ct.nkrow * ct.ncc;
+  int lb = ct.lb;
+  s.pair = (long long)Kab * kPairRec + 4;
+  s.aux = (long long)T * (3 + kAuxRec * Kc);
+  s.loop = per_tg(ct.NV) + per_tg(ct.NW) + per_tg(ct.NF);
+  s.P = per_t(ct.NACC);
+  // region assignment: Y holds P, level 0 (ket out) and even HRR levels;
+  // X holds the loop buffers, the gather output and odd HRR levels.
+  long long Y = std::max(s.P, per_t((int)nK));
+  long long X = std::max(s.loop, per_t((int)nG));
+  for (int j = 1; j <= lb; ++j) {
+    long long sz = per_t(ct.hrows[j] * ct.nC);
+    if (j & 1) X = std::max(X, sz); else Y = std::max(Y, sz);
+  }
+  int cur = (lb & 1) ? 1 : 0;  // 0 = Y, 1 = X
+  int baR = -1, bbR = -1;
+  if (ct.nbA) { cur ^= 1; baR = cur; long long sz = per_t(ct.nbA * ct.nC); if (cur) X = std::max(X, sz); else Y = std::max(Y, sz); }
+  if (ct.nbB) { cur ^= 1; bbR = cur; long long sz = per_t(ct.nbB * ct.nC); if (cur) X = std::max(X, sz); else Y = std::max(Y, sz); }
+  s.Y = Y;
+  s.X = X;
+  s.total = s.pair + s.aux + Y + X;
+  if (!d) return;
+  // fill descriptor layout
+  d->T = T; d->Tp = Tp; d->mode = mode; d->G = G;
+  d->pair_base = 0;
+  d->ab_base = Kab * kPairRec;
+  d->aux_base = (int)s.pair;
+  int ybase = (int)(s.pair + s.aux);
+  int xbase = (int)(ybase + Y);
+  auto mk_t = [&](int base, int n) {
+    Buf b;
+    b.base = base; b.sg = 0;
+    if (mode == 0) { b.si = Tp; b.st = 1; } else { b.si = 1; b.st = n; }
+    return b;
+  };
+  auto mk_tg = [&](int base, int n) {
+    Buf b;
+    b.base = base;
+    if (mode == 0) { b.si = G * Tp; b.sg = Tp; b.st = 1; } else { b.si = 1; b.sg = n; b.st = G * n; }
+    return b;
+  };
+  d->V = mk_tg(xbase, ct.NV);
+  d->W = mk_tg(xbase + (int)per_tg(ct.NV), ct.NW);
+  d->F = mk_tg(xbase + (int)(per_tg(ct.NV) + per_tg(ct.NW)), ct.NF);
+  d->P = mk_t(ybase, ct.NACC);
+  d->Gb = mk_t(xbase, (int)nG);
+  d->H[0] = mk_t(ybase, (int)nK);
+  for (int j = 1; j <= lb; ++j) d->H[j] = mk_t((j & 1) ? xbase : ybase, ct.hrows[j] * ct.nC);
+  Buf last = d->H[lb];
+  if (ct.nbA) { d->BA = mk_t(baR ? xbase : ybase, ct.nbA * ct.nC); last = d->BA; }
+  if (ct.nbB) { d->BB = mk_t(bbR ? xbase : ybase, ct.nbB * ct.nC); last = d->BB; }
+  d->OUT = last;
+  d->smem_doubles = (int)s.total;
+}
+
+}  // namespace
+
+LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit) {
+  const int K = Kab * Kc;
+  const long long budget2 = (smem_limit / 2 - 1024) / 8;  // two CTAs per SM
+  const long long budget1 = (smem_limit - 1024) / 8;
+  LaunchShape best{1, 1, 1, 0};
+  Sizes s;
+  int Ts[] = {128, 64, 32, 16, 8, 4, 2, 1};
+  bool found = false;
+  for (long long budget : {budget2, budget1}) {
+    for (int T : Ts) {
+      if (T > 1 && T > 2 * naux && T != 1) continue;
+      int mode = T >= 32 ? 0 : 1;
+      buffer_sizes(ct, Kab, Kc, T, 1, mode, s, nullptr);
+      if (s.total > budget) continue;
+      // enough independent work per stage?  prefer the largest T that fits
+      int G = 1;
+      int Gmax = std::min(K, 8);
+      while (G < Gmax) {
+        buffer_sizes(ct, Kab, Kc, T, G + 1, mode, s, nullptr);
+        if (s.total > budget) break;
+        ++G;
+      }
+      buffer_sizes(ct, Kab, Kc, T, G, mode, s, nullptr);
+      best = LaunchShape{T, G, mode, (int)(s.total * 8)};
+      found = true;
+      break;
+    }
+    if (found) break;
+  }
+  if (!found) best.smem_bytes = -1;
+  return best;
+}
+
+void fill_layout(ClassDesc& d, const ClassTables& ct, const LaunchShape& sh) {
+  Sizes s;
+  buffer_sizes(ct, d.Kab, d.Kc, sh.T, sh.G, sh.mode, s, &d);
+}
+
+}  // namespace lx3c

@@ -1,0 +1,90 @@
+"""GPU parity: (ab|C) from the CUDA path against the CPU oracle, element by element.
+
+Tolerance (stated by the target): each element within 1e-12 relative or
+1e-14 absolute of the oracle; blocks the FP64 oracle cannot settle are
+recomputed in binary128 (tests/parity.py).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_03192_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from parity import assert_parity  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def lx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_03192_gb300 as m
+    return m
+
+
+def run(lx, p, bra_pure=True):
+    out = lx.eri3c(p.orb, p.aux, p.pairs, p.auxs, bra_pure=bra_pure)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_config1_full(lx):
+    """(pp|d), K=1, 64 pairs x 32 aux shells: every integral."""
+    p = W.config1()
+    assert_parity(run(lx, p), p)
+
+
+SMALL = [(la, lb, lc) for la in range(5) for lb in range(5) for lc in range(7)]
+
+
+@pytest.mark.parametrize("la,lb,lc", SMALL)
+@pytest.mark.parametrize("Kab", [1, 3])
+def test_class_small(lx, la, lb, lc, Kab):
+    """Every (la, lb <= 4 | lc <= 6) class, 5 pairs x 7 aux shells, K_a = K_b = Kab."""
+    p = W.class_problem(la, lb, lc, 5, 7, Kab, Kab, 1, box=6.0, exp_lo=0.1, exp_hi=50.0,
+                        seed=1000 + la * 100 + lb * 10 + lc + 7 * Kab)
+    assert_parity(run(lx, p), p)
+
+
+@pytest.mark.parametrize("la,lb,lc", [(1, 1, 1), (2, 1, 3), (3, 3, 2), (4, 2, 5), (2, 4, 6)])
+def test_cartesian_bra(lx, la, lb, lc):
+    p = W.class_problem(la, lb, lc, 4, 9, 2, 1, 2, box=5.0, exp_lo=0.2, exp_hi=20.0, seed=77 + la + lb + lc)
+    assert_parity(run(lx, p, bra_pure=False), p, bra_pure=False)
+
+
+@pytest.mark.parametrize("la,lb,lc,Ka,Kb,Kc", [(2, 2, 2, 6, 6, 1), (1, 0, 3, 3, 2, 3), (4, 4, 6, 6, 6, 1),
+                                                (0, 0, 0, 6, 6, 4), (3, 1, 4, 1, 6, 2)])
+def test_high_contraction(lx, la, lb, lc, Ka, Kb, Kc):
+    p = W.class_problem(la, lb, lc, 3, 40, Ka, Kb, Kc, box=8.0, exp_lo=0.05, exp_hi=1e4,
+                        seed=300 + la + 10 * lb + 100 * lc)
+    assert_parity(run(lx, p), p)
+
+
+def test_ragged_and_single(lx):
+    """Aux lists that leave a partial last tile, a single pair, a single aux shell."""
+    for (np_, na) in [(1, 1), (1, 33), (2, 129), (3, 257)]:
+        p = W.class_problem(1, 2, 1, np_, na, 2, 1, 1, box=6.0, seed=900 + na)
+        assert_parity(run(lx, p), p)
+        p = W.class_problem(3, 3, 4, np_, na, 1, 1, 1, box=6.0, seed=901 + na)
+        assert_parity(run(lx, p), p)
+
+
+def test_host_path_matches_device(lx):
+    p = W.class_problem(2, 1, 2, 6, 17, 3, 3, 1, box=6.0, seed=55)
+    g = run(lx, p)
+    h = lx.eri3c_host(p.orb, p.aux, p.pairs, p.auxs)
+    np.testing.assert_array_equal(g, h)
+
+
+def test_boys_device(lx):
+    """Device Boys evaluator against the oracle's extended-precision Boys function."""
+    rng = np.random.default_rng(3)
+    T = np.concatenate([np.zeros(1), rng.uniform(0, 1, 200), rng.uniform(0, 40, 400), rng.uniform(40, 130, 300),
+                        10 ** rng.uniform(2, 6, 200), np.arange(0, 117, 0.125), [116.9999999, 117.0, 117.0000001]])
+    mmax = 24
+    g = lx.boys(torch.tensor(T, device="cuda"), mmax).cpu().numpy()
+    ref = np.array([oracle.boys(mmax, t, mode="quad") for t in T])
+    rel = np.abs(g - ref) / np.abs(ref)
+    assert rel.max() < 3e-15, (rel.max(), T[np.unravel_index(rel.argmax(), rel.shape)[0]])

@@ -1,0 +1,119 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The shared library loads, exports every function include/lx3c.h declares,
+validates malformed input before touching the device, and its host-built
+tables agree with the paper's worked CVRR2 expansions (Sec. 2.5.4) and with
+the oracle's independently derived solid harmonics.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.solid import solid_matrix
+import paper_2210_03192_gb300 as lx
+from paper_2210_03192_gb300 import _lib
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lx3c.h")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cvrr2_worked_examples.txt")
+
+
+def declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lx3c_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol():
+    L = _lib.load()
+    names = declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(_lib.EXPORTS), set(names) - set(_lib.EXPORTS)
+
+
+def test_invalid_input_rejected_on_host():
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    l = np.array([1], np.int32)
+    k = np.array([1], np.int32)
+    xyz = np.zeros(3)
+    bad_exp = np.array([-1.0])
+    co = np.array([1.0])
+    rc = L.lx3c_basis_create(ctypes.byref(h), 1, l.ctypes.data, k.ctypes.data, xyz.ctypes.data, None,
+                             bad_exp.ctypes.data, co.ctypes.data, None)
+    assert rc == -1 and b"exponent" in L.lx3c_last_error()
+    big_l = np.array([9], np.int32)
+    rc = L.lx3c_basis_create(ctypes.byref(h), 1, big_l.ctypes.data, k.ctypes.data, xyz.ctypes.data, None,
+                             co.ctypes.data, co.ctypes.data, None)
+    assert rc == -2
+    big_k = np.array([99], np.int32)
+    rc = L.lx3c_basis_create(ctypes.byref(h), 1, l.ctypes.data, big_k.ctypes.data, xyz.ctypes.data, None,
+                             co.ctypes.data, co.ctypes.data, None)
+    assert rc == -2
+    rc = L.lx3c_eri3c_plan(ctypes.byref(h), None, None, None, 0, None, 0, 1, None)
+    assert rc == -1
+    rc = L.lx3c_eri3c_execute(None, None, None)
+    assert rc == -1
+    f = ctypes.c_double()
+    assert L.lx3c_class_flops(-1, 0, 0, 1, 1, 1, ctypes.byref(f)) == -1
+
+
+@pytest.mark.parametrize("l", range(0, 9))
+def test_solid_harmonics_match_oracle(l):
+    np.testing.assert_allclose(lx.solid_harmonics(l), solid_matrix(l), rtol=1e-14, atol=1e-14 * 10 ** (l / 2))
+
+
+def test_cvrr2_worked_examples():
+    for line in open(GOLDEN):
+        if not line.strip() or line.startswith("#"):
+            continue
+        a, c, terms = (p.strip() for p in line.split("|"))
+        vec = lambda s: tuple(int(x) for x in s.split(","))
+        ref = {}
+        for t in terms.split():
+            coef, e, kk, n = t.split(":")
+            ref[(vec(e), int(kk), vec(n))] = float(coef)
+        assert lx.cvrr2_expansion(vec(a), vec(c)) == ref
+
+
+def test_cvrr2_closed_form_all_targets():
+    """The library's tabulated n-q expansion equals the closed form for every
+    (a, c) up to |a| = 8, |c| = 6."""
+    from math import comb, factorial
+    from oracle.solid import cart_list
+    for la in (0, 3, 8):
+        for lc in (0, 2, 6):
+            for a in cart_list(la):
+                for c in cart_list(lc):
+                    ref = {}
+                    for ux in range(min(a[0], c[0]) + 1):
+                        for uy in range(min(a[1], c[1]) + 1):
+                            for uz in range(min(a[2], c[2]) + 1):
+                                u = (ux, uy, uz)
+                                coef = 1
+                                for i in range(3):
+                                    coef *= comb(a[i], u[i]) * comb(c[i], u[i]) * factorial(u[i])
+                                key = (tuple(a[i] - u[i] for i in range(3)), sum(u),
+                                       tuple(c[i] - u[i] for i in range(3)))
+                                ref[key] = ref.get(key, 0) + coef
+                    assert lx.cvrr2_expansion(a, c) == {k: float(v) for k, v in ref.items()}
+
+
+def test_class_flops_scale_with_contraction():
+    f1 = lx.class_flops(4, 4, 6, 1)
+    f2 = lx.class_flops(4, 4, 6, 2)
+    f36 = lx.class_flops(4, 4, 6, 36)
+    assert f36 - f1 == pytest.approx(35 * (f2 - f1))   # per-primitive work is linear in K
+    assert lx.class_flops(0, 0, 0, 1) < lx.class_flops(1, 0, 0, 1) < lx.class_flops(1, 1, 0, 1)
+
+
+def test_device_calls_fail_loudly_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(lx.LibraryError):
+        lx.boys(torch.zeros(3, dtype=torch.float64), 4)
