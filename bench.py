@@ -243,26 +243,27 @@ def run_e2e(plans, args):
 # ---------------------------------------------------------------------------
 
 def oracle_sample(classes, args, seconds):
-    """Time the oracle on a bounded sample of the sweep: the first pair against
-    the first n ket shells of every class, n grown until ~`seconds` of work."""
+    """Time the oracle (as it stands, FP64 mode) on a bounded sample of the
+    sweep: the first np pairs against the first 64 ket shells of every class,
+    np doubled until the sample takes about `seconds` of host time."""
     import oracle
     from paper_2210_03192_gb300 import workloads as W
     oracle.build()
-    probs = [W.config2_class(la, lb, lc, K, 1, 64, product_reading=args.product_k) for (la, lb, lc, K) in classes]
-    n = 1
+    probs = [W.config2_class(la, lb, lc, K, 64, 64, product_reading=args.product_k) for (la, lb, lc, K) in classes]
+    npr = 1
     while True:
         t0 = time.perf_counter()
         ints = 0
         for p in probs:
-            X = oracle.eri3c(p.orb, p.aux, p.pairs[:1], p.auxs[:n], bra_pure=True)
+            X = oracle.eri3c(p.orb, p.aux, p.pairs[:npr], p.auxs, bra_pure=True)
             ints += X.size
         dt = time.perf_counter() - t0
-        if dt >= seconds / 4 or n >= 64:
+        if dt >= seconds / 3 or npr >= 64:
             break
-        n = min(64, max(n * 2, int(n * seconds / 4 / max(dt, 1e-3))))
+        npr = min(64, max(npr * 2, int(npr * seconds / max(dt, 1e-3))))
     return dict(value=round(ints / dt / 1e9, 6), unit="Gints/s", cores=oracle.num_threads(), kind="oracle",
-                sample="1 pair x %d ket shells of each of %d classes (%d integrals), McMurchie-Davidson FP64, "
-                       "%.1f s" % (n, len(probs), ints, dt), seconds=dt, ints=ints)
+                sample="%d pairs x 64 ket shells of each of %d classes (%d integrals), McMurchie-Davidson FP64, "
+                       "%.1f s" % (npr, len(probs), ints, dt), seconds=dt, ints=ints)
 
 
 def run_reference(args, rank, world):

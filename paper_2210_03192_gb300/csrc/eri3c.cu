@@ -54,6 +54,17 @@ __device__ __forceinline__ double rsqrt_fp64(double x) {
   return fma(q, p, y0);
 }
 
+// 1/x for x > 0 in FP64: single-precision seed, then two Newton-Raphson steps
+// r <- r (2 - x r) written as e = 1 - x r, r <- r + r e (quadratic
+// convergence: ~1e-7 -> ~1e-14 -> rounding level).
+__device__ __forceinline__ double rcp_fp64(double x) {
+  double r = (double)__frcp_rn(__double2float_rn(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // pref * F_m(T) for m = hi down to lo, written to v[(m - lo) * stride].
 // F_hi and exp(-T) come from the interpolation table (T < 117) or the
 // asymptotic form (T >= 117, exp(-T) = 0); lower orders by the downward
@@ -77,7 +88,7 @@ __device__ __forceinline__ void boys_scaled(const double* __restrict__ tab, cons
     }
   } else {
     double rs = rsqrt_fp64(T);
-    double b = rs * rs;
+    double b = rcp_fp64(T);
     double p = rs;
     int e = hi;
     while (e) {

@@ -87,4 +87,8 @@ def test_boys_device(lx):
     g = lx.boys(torch.tensor(T, device="cuda"), mmax).cpu().numpy()
     ref = np.array([oracle.boys(mmax, t, mode="quad") for t in T])
     rel = np.abs(g - ref) / np.abs(ref)
-    assert rel.max() < 3e-15, (rel.max(), T[np.unravel_index(rel.argmax(), rel.shape)[0]])
+    # interpolation region: a few ulp; T >= 117: F_24 = Gamma(24.5)/2 T^-24.5 by
+    # 24 multiplications, about one ulp each
+    small = T < 117.0
+    assert rel[small].max() < 3e-15, (rel[small].max(), T[small][np.unravel_index(rel[small].argmax(), rel[small].shape)[0]])
+    assert rel[~small].max() < 6e-15, (rel[~small].max(), T[~small][np.unravel_index(rel[~small].argmax(), rel[~small].shape)[0]])
