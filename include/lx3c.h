@@ -156,6 +156,39 @@ lx3c_status lx3c_solid_harmonics(int l, double* out);
 lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap, double* terms,
                                  int32_t* nterms);
 
+/*
+ * Allocation-free form of one (la lb|lc) class evaluation.  The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory
+ * around the call -- for example code that runs while a memory pool owns the
+ * device heap (a raw cudaMalloc then fails or fragments the pool) or code that
+ * must not stall the device (cudaFree synchronises the whole device).
+ *
+ * Inputs and the output are the caller's, all device pointers:
+ *   la, lb, lc, ka, kb, kc  the class and contraction degrees; every pair in
+ *                           `pairs` must have an l=la, k=ka first shell and an
+ *                           l=lb, k=kb second shell, every ket shell in `auxs`
+ *                           l=lc, k=kc (not checked: the lists stay on the device)
+ *   *_off, *_xyz, *_exps, *_coefs  shell tables as in lx3c_basis_create
+ *                           (off[s] = index of shell s's first primitive)
+ *   pairs[2*npair], auxs[naux]  shell indices; out: npair*naux*nA*nB*nC
+ *                           doubles, same layout as lx3c_eri3c_execute.
+ * Everything else the path needs (primitive records, sub-pair lists, Boys
+ * and index tables) lives in one statically sized device array of about
+ * 27 MB that every GPU loading the library holds until process exit.
+ * Limits: npair <= 65536, npair*ka*kb <= 65536, naux*kc <= 65536; larger
+ * problems are rejected with LX3C_ENOTSUP and nothing is launched.
+ * The first call on a device copies the Boys table into that array
+ * (synchronously); make that first call before any stream capture.  All calls
+ * share the array and each overwrites it: calls that overlap on the GPU (for
+ * instance on different streams) race; calls on one stream are ordered.
+ * Asynchronous on `stream` otherwise; no device memory is allocated or freed.
+ */
+lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb, int kc, int bra_pure,
+                               const int64_t* orb_off, const double* orb_xyz, const double* orb_exps,
+                               const double* orb_coefs, const int64_t* aux_off, const double* aux_xyz,
+                               const double* aux_exps, const double* aux_coefs, const int32_t* pairs,
+                               int64_t npair, const int32_t* auxs, int64_t naux, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,8 @@ EXPORTS = {
     "lx3c_class_flops": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, c_f64p]),
     "lx3c_solid_harmonics": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
+    "lx3c_eri3c_noalloc": (ctypes.c_int, [ctypes.c_int] * 7 + [ctypes.c_void_p] * 9 + [ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lx3c_cvrr2_expansion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int32)]),
 }

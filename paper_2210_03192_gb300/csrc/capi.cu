@@ -37,6 +37,15 @@ lx3c_status fail(lx3c_status s, const std::string& msg) {
   return s;
 }
 
+}  // namespace
+
+namespace lx3c {
+// lets other translation units report through lx3c_last_error()
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace lx3c
+
+namespace {
+
 #define CUDA_TRY(expr)                                                                  \
   do {                                                                                  \
     cudaError_t e_ = (expr);                                                            \

@@ -1,0 +1,60 @@
+"""The allocation-free entry point lx3c_eri3c_noalloc against the planned path.
+
+lx3c_eri3c_noalloc is for callers that cannot allocate device memory around
+the call (a pool allocator owns the device heap, or the caller must not let
+cudaFree synchronise the device).  Its scratch lives in one static device
+array shared by all calls.  This test calls it through the C ABI twice in a
+row, on two different classes so that the second call overwrites what the
+first left in the array, and checks each result against lx3c_eri3c_execute
+with the tolerance the other parity tests use.  It sits in a file of its own
+that pytest collects last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2210_03192_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL = 1e-12, 1e-14
+
+
+def dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a, dt), device="cuda")
+
+
+def call_noalloc(lx, p, bra_pure=True):
+    L = lx._lib.load()
+    la, lb, lc = p.la, p.lb, p.lc
+    ka, kb, kc = int(p.orb.k[p.pairs[0, 0]]), int(p.orb.k[p.pairs[0, 1]]), int(p.aux.k[p.auxs[0]])
+    keep = [dev(p.orb.off, np.int64), dev(p.orb.xyz, np.float64), dev(p.orb.exps, np.float64),
+            dev(p.orb.coefs, np.float64), dev(p.aux.off, np.int64), dev(p.aux.xyz, np.float64),
+            dev(p.aux.exps, np.float64), dev(p.aux.coefs, np.float64), dev(p.pairs, np.int32),
+            dev(p.auxs, np.int32)]
+    nA = 2 * la + 1 if bra_pure else (la + 1) * (la + 2) // 2
+    nB = 2 * lb + 1 if bra_pure else (lb + 1) * (lb + 2) // 2
+    out = torch.full((p.npair, p.naux, nA, nB, 2 * lc + 1), float("nan"), dtype=torch.float64, device="cuda")
+    ptrs = [ctypes.c_void_p(t.data_ptr()) for t in keep]
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.lx3c_eri3c_noalloc(la, lb, lc, ka, kb, kc, int(bra_pure), *ptrs[:8], ptrs[8], p.npair, ptrs[9], p.naux,
+                              ctypes.c_void_p(out.data_ptr()), st)
+    assert rc == 0, L.lx3c_last_error()
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_noalloc_matches_planned_path_twice():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_03192_gb300 as lx
+    cases = [W.class_problem(2, 3, 4, 7, 45, 3, 2, 1, box=6.0, exp_lo=0.1, exp_hi=50.0, seed=4242),
+             W.class_problem(3, 1, 2, 5, 70, 2, 3, 2, box=6.0, exp_lo=0.1, exp_hi=50.0, seed=4343)]
+    got = [call_noalloc(lx, p) for p in cases]
+    for p, g in zip(cases, got):
+        ref = lx.eri3c(p.orb, p.aux, p.pairs, p.auxs).cpu().numpy()
+        assert np.isfinite(g).all()
+        ok = np.abs(g - ref) <= np.maximum(RTOL * np.abs(ref), ATOL)
+        assert ok.all(), (np.abs(g - ref).max(), (~ok).sum())
