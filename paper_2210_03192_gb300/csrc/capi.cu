@@ -378,22 +378,57 @@ lx3c_status lx3c_eri3c_plan(lx3c_plan** out, const lx3c_basis* orb, const lx3c_b
     const ClassTables& ct = class_tables(la, lb, lc, p->bra_pure);
     p->nblk = (int64_t)ct.nA * ct.nB * ct.nC;
   }
-  // Orientation of every primitive pair: the recurrences run on the more
-  // compact centre (larger exponent), so that HRR transfers quanta towards
-  // the centre farther from P and never cancels (diffuse A with compact B
-  // would otherwise lose up to all FP64 digits).  Without HRR (lb = 0) every
-  // primitive pair keeps the caller's orientation.
+  // Orientation.  HRR (Eq. hrr) builds the target centre's quanta from the
+  // recurrence centre's through AB; when the target is compact and the
+  // recurrence centre diffuse, P sits near the target and the transfer
+  // cancels, amplifying FP64 rounding by about
+  //   amp = ((|AB| + s) / (|P - target| + s))^l_target,  s = 1/sqrt(2 gamma),
+  // weighted by the primitive pair's share of the largest prefactor
+  // |c_a c_b exp(-za zb/gamma AB^2)/gamma| in the pair.  A pair keeps one
+  // orientation (the one with the smaller worst weighted amp) when that worst
+  // amp is below kAmpMax; otherwise every primitive pair runs on its more
+  // compact centre (two launches, the second accumulating transposed).
+  // Without HRR (lb = 0) the caller's orientation is always kept.
+  const double kAmpMax = 300.0;
   std::vector<int4> subA, subB;
   std::vector<int> primA, primB;
   int kA = 0, kB = 0;
+  std::vector<double> wgt(Ka * Kb), ampA(Ka * Kb), ampB(Ka * Kb);
   for (int64_t i = 0; i < npair; ++i) {
     int32_t a = pairs[2 * i], b = pairs[2 * i + 1];
+    const double* A = &orb->xyz[3 * a];
+    const double* B = &orb->xyz[3 * b];
+    double ab2 = 0;
+    for (int x = 0; x < 3; ++x) ab2 += (A[x] - B[x]) * (A[x] - B[x]);
+    const double dab = std::sqrt(ab2);
+    double wmax = 0;
+    for (int ia = 0; ia < Ka; ++ia)
+      for (int ib = 0; ib < Kb; ++ib) {
+        double za = orb->exps[orb->off[a] + ia], zb = orb->exps[orb->off[b] + ib], g = za + zb;
+        double w = std::fabs(orb->coefs[orb->off[a] + ia] * orb->coefs[orb->off[b] + ib]) *
+                   std::exp(-za * zb / g * ab2) / g;
+        double sg = 1.0 / std::sqrt(2.0 * g);
+        // recurrences on A: quanta moved to B (distance |P-B| = za/g |AB|); on B: to A
+        ampA[ia * Kb + ib] = std::pow((dab + sg) / (za / g * dab + sg), lb);
+        ampB[ia * Kb + ib] = std::pow((dab + sg) / (zb / g * dab + sg), la);
+        wgt[ia * Kb + ib] = w;
+        wmax = std::max(wmax, w);
+      }
+    double worstA = 0, worstB = 0;
+    for (int r = 0; r < Ka * Kb; ++r) {
+      double f = wmax > 0 ? wgt[r] / wmax : 1.0;
+      worstA = std::max(worstA, ampA[r] * f);
+      worstB = std::max(worstB, ampB[r] * f);
+    }
     int oa = (int)primA.size(), ob = (int)primB.size();
     for (int ia = 0; ia < Ka; ++ia)
       for (int ib = 0; ib < Kb; ++ib) {
-        double za = orb->exps[orb->off[a] + ia], zb = orb->exps[orb->off[b] + ib];
-        bool onB = lb > 0 && zb > za;
-        (onB ? primB : primA).push_back(ia * Kb + ib);
+        const int r = ia * Kb + ib;
+        bool onB;
+        if (lb == 0) onB = false;
+        else if (std::min(worstA, worstB) <= kAmpMax) onB = worstB < worstA;
+        else onB = orb->exps[orb->off[b] + ib] > orb->exps[orb->off[a] + ia];
+        (onB ? primB : primA).push_back(r);
       }
     int na = (int)primA.size() - oa, nb = (int)primB.size() - ob;
     if (na) subA.push_back(int4{(int)i, oa, na, 0});

@@ -360,22 +360,31 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
         __syncthreads();
       }
       if (Lab == 0) __syncthreads();
-      // ---- accumulate CVRR2 prerequisites over the chunk's primitives
+      // ---- accumulate CVRR2 prerequisites over the chunk's primitives; two
+      // independent accumulators per thread keep two FMA chains in flight
       {
         FDiv fX;
         fX.init(d.NACC);
         const unsigned n = (unsigned)(T * d.NACC);
-        for (unsigned w = tid; w < n; w += kThreads) {
-          int t, a;
-          dec2(w, mode, fT, fX, t, a);
-          if (t >= tv) continue;
-          const unsigned e = __ldg(d.atab + a);
-          const int vi = e & 0xFFFF, wi = e >> 16;
-          const int pa = BUF_T(d.P, a, t);
-          double acc = sm[pa];
-          int vb = BUF_TG(d.V, vi, 0, t), wb = BUF_TG(d.W, wi, 0, t);
-          for (int g = 0; g < gcnt; ++g) acc = fma(sm[vb + g * d.V.sg], sm[wb + g * d.W.sg], acc);
-          sm[pa] = acc;
+        for (unsigned w0 = tid; w0 < n; w0 += 2 * kThreads) {
+          const unsigned w1 = w0 + kThreads;
+          const bool has1 = w1 < n;
+          int t0, a0, t1, a1;
+          dec2(w0, mode, fT, fX, t0, a0);
+          dec2(has1 ? w1 : w0, mode, fT, fX, t1, a1);
+          const bool ok0 = t0 < tv, ok1 = has1 && t1 < tv;
+          const unsigned e0 = __ldg(d.atab + a0), e1 = __ldg(d.atab + a1);
+          const int pa0 = BUF_T(d.P, a0, t0), pa1 = BUF_T(d.P, a1, t1);
+          const int vb0 = BUF_TG(d.V, (int)(e0 & 0xFFFF), 0, t0), wb0 = BUF_TG(d.W, (int)(e0 >> 16), 0, t0);
+          const int vb1 = BUF_TG(d.V, (int)(e1 & 0xFFFF), 0, t1), wb1 = BUF_TG(d.W, (int)(e1 >> 16), 0, t1);
+          double acc0 = sm[pa0], acc1 = sm[pa1];
+#pragma unroll 4
+          for (int g = 0; g < gcnt; ++g) {
+            acc0 = fma(sm[vb0 + g * d.V.sg], sm[wb0 + g * d.W.sg], acc0);
+            acc1 = fma(sm[vb1 + g * d.V.sg], sm[wb1 + g * d.W.sg], acc1);
+          }
+          if (ok0) sm[pa0] = acc0;
+          if (ok1) sm[pa1] = acc1;
         }
       }
       __syncthreads();
@@ -393,6 +402,7 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
         const int id = __ldg(d.gdst + r);
         const int q0 = __ldg(d.gptr + id), q1 = __ldg(d.gptr + id + 1);
         double s = 0.0;
+#pragma unroll 4
         for (int q = q0; q < q1; ++q) {
           const unsigned e = __ldg(d.gterm + q);
           s = fma(__ldg(d.pal + (e >> 20)), sm[BUF_T(d.P, e & 0xFFFFF, t)], s);

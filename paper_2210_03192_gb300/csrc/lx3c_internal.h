@@ -8,7 +8,7 @@
 
 namespace lx3c {
 
-constexpr int kThreads = 256;            // threads per CTA of the integral kernels
+constexpr int kThreads = 512;            // threads per CTA of the integral kernels
 constexpr int kMaxLev = 16;              // VRR1 levels (la+lb) and HRR levels (lb)
 constexpr int kPairRec = 28;             // doubles per primitive-pair record
 constexpr int kPairNHalf = 13;           // offset of n/(2 gamma), n = 1..14

@@ -62,21 +62,45 @@ std::mutex g_na_mu;
 std::map<int, unsigned char*> g_na_base;  // per device: scratch address, set up once
 std::vector<double> g_na_boys, g_na_mid;
 
-// Split every primitive pair of every pair by orientation (recurrences on the
-// more compact centre, as the planned path does) into two sub-pair lists with
-// fixed slots: sub-pair p of list o holds its primitive indices at
-// prim[o][p*kab ...].  List 1 always accumulates onto list 0's store.
-__global__ void noalloc_orient(const int32_t* __restrict__ pairs, long long npair, int ka, int kb, int split,
-                               const int64_t* __restrict__ off, const double* __restrict__ exps,
+// Split the primitive pairs of every pair by orientation with the planned
+// path's rule (lx3c_eri3c_plan): a pair keeps one orientation when its worst
+// weighted HRR amplification there is at most amp_max, otherwise each
+// primitive pair runs on its more compact centre.  Sub-pair p of list o holds
+// its primitive indices at prim[o][p*kab ...]; list 1 always accumulates onto
+// list 0's store.
+__global__ void noalloc_orient(const int32_t* __restrict__ pairs, long long npair, int la, int lb, int ka, int kb,
+                               const int64_t* __restrict__ off, const double* __restrict__ xyz,
+                               const double* __restrict__ exps, const double* __restrict__ coefs, double amp_max,
                                int4* __restrict__ sub, int* __restrict__ prim) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= npair) return;
   const int kab = ka * kb;
   const int sa = pairs[2 * p], sb = pairs[2 * p + 1];
+  double ab2 = 0;
+  for (int x = 0; x < 3; ++x) ab2 += (xyz[3 * sa + x] - xyz[3 * sb + x]) * (xyz[3 * sa + x] - xyz[3 * sb + x]);
+  const double dab = sqrt(ab2);
+  double wmax = 0;
+  for (int ia = 0; ia < ka; ++ia)
+    for (int ib = 0; ib < kb; ++ib) {
+      const double za = exps[off[sa] + ia], zb = exps[off[sb] + ib], g = za + zb;
+      wmax = fmax(wmax, fabs(coefs[off[sa] + ia] * coefs[off[sb] + ib]) * exp(-za * zb / g * ab2) / g);
+    }
+  double worstA = 0, worstB = 0;
+  for (int ia = 0; ia < ka; ++ia)
+    for (int ib = 0; ib < kb; ++ib) {
+      const double za = exps[off[sa] + ia], zb = exps[off[sb] + ib], g = za + zb;
+      const double w = fabs(coefs[off[sa] + ia] * coefs[off[sb] + ib]) * exp(-za * zb / g * ab2) / g;
+      const double f = wmax > 0 ? w / wmax : 1.0, sg = 1.0 / sqrt(2.0 * g);
+      worstA = fmax(worstA, pow((dab + sg) / (za / g * dab + sg), (double)lb) * f);
+      worstB = fmax(worstB, pow((dab + sg) / (zb / g * dab + sg), (double)la) * f);
+    }
   int na = 0, nb = 0;
   for (int ia = 0; ia < ka; ++ia)
     for (int ib = 0; ib < kb; ++ib) {
-      const bool onB = split && exps[off[sb] + ib] > exps[off[sa] + ia];
+      bool onB;
+      if (lb == 0) onB = false;
+      else if (fmin(worstA, worstB) <= amp_max) onB = worstB < worstA;
+      else onB = exps[off[sb] + ib] > exps[off[sa] + ia];
       if (onB) prim[(npair + p) * kab + nb++] = ia * kb + ib;
       else prim[p * kab + na++] = ia * kb + ib;
     }
@@ -175,8 +199,8 @@ extern "C" lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb
   e = launch_pair_precompute(orb, pairs, npair, ka, kb, pairrec, pairab, st);
   if (e == cudaSuccess) e = launch_aux_precompute(aux, auxs, naux, kc, auxrec, auxc, st);
   if (e == cudaSuccess) {
-    noalloc_orient<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pairs, npair, ka, kb, split, orb_off, orb_exps,
-                                                                     sub, prim);
+    noalloc_orient<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pairs, npair, la, lb, ka, kb, orb_off, orb_xyz,
+                                                                     orb_exps, orb_coefs, 300.0, sub, prim);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return na_fail(LX3C_ECUDA, cudaGetErrorString(e));

@@ -479,7 +479,7 @@ LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux,
   const long long budget1 = (smem_limit - 1024) / 8;
   LaunchShape best{1, 1, 1, 0};
   Sizes s;
-  int Ts[] = {128, 64, 32, 16, 8, 4, 2, 1};
+  int Ts[] = {512, 256, 128, 64, 32, 16, 8, 4, 2, 1};
   bool found = false;
   for (long long budget : {budget2, budget1}) {
     for (int T : Ts) {
@@ -495,6 +495,9 @@ LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux,
         if (s.total > budget) break;
         ++G;
       }
+      // balance the primitive chunks: same number of chunks, equal sizes
+      const int nch = (K + G - 1) / G;
+      G = (K + nch - 1) / nch;
       buffer_sizes(ct, Kab, Kc, T, G, mode, s, nullptr);
       best = LaunchShape{T, G, mode, (int)(s.total * 8)};
       found = true;
