@@ -57,6 +57,7 @@ typedef int lx3c_status;
 
 typedef struct lx3c_basis lx3c_basis;
 typedef struct lx3c_plan lx3c_plan;
+typedef struct lx3c_dfj lx3c_dfj;
 
 /* Thread-local description of the last failure in this thread. */
 const char* lx3c_last_error(void);
@@ -155,6 +156,42 @@ lx3c_status lx3c_solid_harmonics(int l, double* out);
  */
 lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap, double* terms,
                                  int32_t* nterms);
+
+/*
+ * Density-fitted Coulomb build (paper Sec. 3: the DF-J builder fed by an
+ * integral-digestion callable; integrals never reach global memory):
+ *   gamma_P = sum_{mu nu} (mu nu|P) D_{mu nu},   J_{mu nu} = sum_P (mu nu|P) c_P
+ * over all AO pairs of the orbital basis (all shells solid harmonic, AO order =
+ * shell order, components m = -l..l), for every ket shell P of the aux basis.
+ *
+ * lx3c_dfj_plan: setup (synchronises `stream`, not part of the timed path).
+ *   Screening: a (pair, ket) triple is kept when Q_ab Q_P >= schwarz_tol, with
+ *   Q_ab = sum over primitive pairs of |c_a c_b| exp(-za zb/g AB^2)
+ *   sqrt(2 pi^{5/2}/(g^2 sqrt(2g))) (|PA|^2+1/(2g))^{la/2} (|PB|^2+1/(2g))^{lb/2}
+ *   and Q_P = sum |c_c| sqrt(2 pi^{5/2}/(z^2 sqrt(2z))) (1/(2z))^{lc/2}, an
+ *   estimate of sqrt(max|(ab|ab)|) and sqrt(max|(P|P)|).  Pass 0 to keep all.
+ *   Returns LX3C_ENOTSUP for orbital shells above LX3C_LMAX_ORB.
+ * lx3c_dfj_execute: D (device, nao x nao row-major, symmetric), c (device,
+ *   naux_ao) in; gamma (device, naux_ao) and J (device, nao x nao, symmetric)
+ *   overwritten.  Asynchronous on `stream`.  Summation order inside gamma and J
+ *   follows FP64 atomic arrival order.
+ * lx3c_dfj_info: out[0..6] = groups, screened (pair, ket shell) triples,
+ *   integrals digested, algorithmic FP64 flops per execute, kernel launches
+ *   per execute, nao, naux_ao.
+ * lx3c_dfj_group: the screened task list of class group gi (for checks):
+ *   info[8] = {la, lb, lc, ka, kb, kc, npair, nket}; pairs[2*npair] shell
+ *   indices (a, b); counts[npair]: pair i is kept with the first counts[i]
+ *   entries of auxs[nket] (ket shells sorted by decreasing Q_P).  Any output
+ *   pointer may be NULL.
+ */
+lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basis* aux, double schwarz_tol,
+                          void* stream);
+lx3c_status lx3c_dfj_execute(lx3c_dfj* plan, const double* D, const double* c, double* gamma, double* J,
+                             void* stream);
+lx3c_status lx3c_dfj_info(const lx3c_dfj* plan, double* out, int n);
+lx3c_status lx3c_dfj_group(const lx3c_dfj* plan, int gi, int32_t* info, int32_t* pairs, int32_t* counts,
+                           int32_t* auxs);
+void lx3c_dfj_destroy(lx3c_dfj* plan);
 
 /*
  * Allocation-free form of one (la lb|lc) class evaluation.  The paper has no

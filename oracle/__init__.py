@@ -235,7 +235,7 @@ def ao_offsets(basis, pure=True):
     return off
 
 
-def dfj(orb, aux, D, c, tasks=None, extended=False):
+def dfj(orb, aux, D, c, tasks=None, extended=False, mode="double"):
     """gamma_P and J_mn over ALL AO pairs (mu, nu) of a pure orbital basis.
 
     tasks: optional list of (shell_a, shell_b, aux_shell) with shell_a <= shell_b
@@ -248,7 +248,7 @@ def dfj(orb, aux, D, c, tasks=None, extended=False):
     if tasks is None:
         tasks = [(i, j, P) for i in range(nsh) for j in range(i, nsh) for P in range(len(aux.l))]
     tasks = np.asarray(tasks, np.int64).reshape(-1, 3)
-    blocks = eri3c_triples(orb, aux, tasks[:, :2], tasks[:, 2], bra_pure=True, extended=extended)
+    blocks = eri3c_triples(orb, aux, tasks[:, :2], tasks[:, 2], bra_pure=True, extended=extended, mode=mode)
     gamma = np.zeros(int(aq[-1]))
     J = np.zeros((int(ao[-1]), int(ao[-1])))
     for (i, j, P), X in zip(tasks, blocks):

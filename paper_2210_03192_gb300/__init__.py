@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import LibraryError, check, ptr
 from . import workloads  # noqa: F401  (seeded input generators)
 
-__all__ = ["DeviceBasis", "Eri3cPlan", "eri3c", "eri3c_host", "boys", "class_flops", "solid_harmonics",
+__all__ = ["DeviceBasis", "Eri3cPlan", "DFJPlan", "eri3c", "eri3c_host", "boys", "class_flops", "solid_harmonics",
            "cvrr2_expansion", "LibraryError", "workloads"]
 
 
@@ -142,6 +142,67 @@ def eri3c_host(orb, aux, pairs, auxs, bra_pure=True, out=None, stream=None):
                             a(aux.coefs, np.float64), ptr(pairs), len(pairs), ptr(auxs), len(auxs),
                             int(bool(bra_pure)), ptr(out), st), "lx3c_eri3c_host")
     return out
+
+
+class DFJPlan:
+    """Screened DF-J build (lx3c_dfj): gamma_P and J_mn from D and c, Sec. 3."""
+
+    def __init__(self, orb, aux, schwarz_tol=1e-12, stream=None):
+        L = _lib.load()
+        self.orb = orb if isinstance(orb, DeviceBasis) else DeviceBasis(orb, stream)
+        self.aux = aux if isinstance(aux, DeviceBasis) else DeviceBasis(aux, stream)
+        self.handle = ctypes.c_void_p()
+        check(L.lx3c_dfj_plan(ctypes.byref(self.handle), self.orb.handle, self.aux.handle, float(schwarz_tol),
+                              _stream_handle(stream)), "lx3c_dfj_plan")
+        info = np.zeros(7)
+        check(L.lx3c_dfj_info(self.handle, ptr(info), 7), "lx3c_dfj_info")
+        self.ngroups, self.ntasks, self.nint, self.flops, self.launches, self.nao, self.naux_ao = (
+            int(info[0]), int(info[1]), float(info[2]), float(info[3]), int(info[4]), int(info[5]), int(info[6]))
+
+    def execute(self, D, c, gamma=None, J=None, stream=None):
+        torch = _torch()
+        for name, t, n in (("D", D, self.nao * self.nao), ("c", c, self.naux_ao)):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise LibraryError("DFJPlan.execute: %s must be a contiguous float64 CUDA tensor of %d" % (name, n))
+        if gamma is None:
+            gamma = torch.empty(self.naux_ao, dtype=torch.float64, device=D.device)
+        if J is None:
+            J = torch.empty((self.nao, self.nao), dtype=torch.float64, device=D.device)
+        check(_lib.load().lx3c_dfj_execute(self.handle, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                           ctypes.c_void_p(gamma.data_ptr()), ctypes.c_void_p(J.data_ptr()),
+                                           _stream_handle(stream)), "lx3c_dfj_execute")
+        return gamma, J
+
+    def groups(self):
+        """Screened task list: list of dicts (class, pairs[n,2], counts[n], auxs[m])."""
+        L = _lib.load()
+        out = []
+        for g in range(self.ngroups):
+            info = np.zeros(8, np.int32)
+            check(L.lx3c_dfj_group(self.handle, g, ptr(info), None, None, None), "lx3c_dfj_group")
+            npair, nket = int(info[6]), int(info[7])
+            pairs = np.zeros((npair, 2), np.int32)
+            counts = np.zeros(npair, np.int32)
+            auxs = np.zeros(nket, np.int32)
+            check(L.lx3c_dfj_group(self.handle, g, None, ptr(pairs), ptr(counts), ptr(auxs)), "lx3c_dfj_group")
+            out.append(dict(cls=tuple(int(x) for x in info[:6]), pairs=pairs, counts=counts, auxs=auxs))
+        return out
+
+    def tasks(self):
+        """All screened (a, b, P) triples as an int array [n, 3]."""
+        rows = []
+        for g in self.groups():
+            for (a, b), n in zip(g["pairs"], g["counts"]):
+                t = np.empty((n, 3), np.int64)
+                t[:, 0], t[:, 1], t[:, 2] = a, b, g["auxs"][:n]
+                rows.append(t)
+        return np.concatenate(rows) if rows else np.zeros((0, 3), np.int64)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.lx3c_dfj_destroy(h)
+            self.handle = None
 
 
 def boys(T, mmax, stream=None):

@@ -42,6 +42,12 @@ EXPORTS = {
     "lx3c_solid_harmonics": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
     "lx3c_eri3c_noalloc": (ctypes.c_int, [ctypes.c_int] * 7 + [ctypes.c_void_p] * 9 + [ctypes.c_int64,
                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    "lx3c_dfj_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_double, ctypes.c_void_p]),
+    "lx3c_dfj_execute": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "lx3c_dfj_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "lx3c_dfj_group": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
+    "lx3c_dfj_destroy": (None, [ctypes.c_void_p]),
     "lx3c_cvrr2_expansion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int32)]),
 }

@@ -52,32 +52,18 @@ namespace {
     if (e_ != cudaSuccess) return fail(LX3C_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// Per-device constant data: Boys tables and uploaded class tables.
-struct DevClass {
-  void* blob = nullptr;
-  const uint4* vtab;
-  const int4* wtab;
-  const unsigned* atab;
-  const int* gptr;
-  const unsigned* gterm;
-  const int* gdst;
-  const double* pal;
-  const int* kptr;
-  const int2* kent;
-  const int4* htab;
-  const int* baptr;
-  const int2* baent;
-  const int* bbptr;
-  const int2* bbent;
-};
+}  // namespace
 
-struct DevState {
+// Per-device constant data: Boys tables and uploaded class tables.
+struct lx3c::DevState {
   double* boys_tab = nullptr;
   double* boys_mid = nullptr;
   int nsm = 0;
   int smem_per_sm = 0;
   std::map<std::tuple<int, int, int, int>, DevClass> classes;
 };
+
+namespace {
 
 std::mutex g_mu;
 std::map<int, DevState> g_dev;
@@ -149,19 +135,100 @@ lx3c_status device_class(DevState* s, const ClassTables& ct, DevClass** out) {
 
 }  // namespace
 
-struct lx3c_basis {
-  int64_t nshell = 0, nprim = 0;
-  std::vector<int32_t> l, k, atom;
-  std::vector<int64_t> off;
-  std::vector<double> xyz, exps, coefs;
-  int32_t* d_l = nullptr;
-  int32_t* d_k = nullptr;
-  int64_t* d_off = nullptr;
-  double* d_xyz = nullptr;
-  double* d_exps = nullptr;
-  double* d_coefs = nullptr;
-  DevBasis dev() const { return DevBasis{d_l, d_k, d_off, d_xyz, d_exps, d_coefs}; }
-};
+namespace lx3c {
+
+int device_state_get(DevState** out) { return device_state(out); }
+int device_class_get(DevState* s, const ClassTables& ct, DevClass** out) { return device_class(s, ct, out); }
+const double* dev_boys_tab(const DevState* s) { return s->boys_tab; }
+const double* dev_boys_mid(const DevState* s) { return s->boys_mid; }
+int dev_nsm(const DevState* s) { return s->nsm; }
+int dev_smem(const DevState* s) { return s->smem_per_sm; }
+
+int fill_class_desc(ClassDesc& d, const ClassTables& ct, const DevClass& dc, const DevState* ds, int orient,
+                    int kmax, int Kab_rec, int Kc, long long naux_for_shape) {
+  LaunchShape sh = choose_shape(ct, kmax, Kc, naux_for_shape, ds->smem_per_sm);
+  if (sh.smem_bytes < 0 || sh.smem_bytes > 232448) return -1;
+  std::memset(&d, 0, sizeof(d));
+  d.la = ct.la; d.lb = ct.lb; d.lc = ct.lc; d.Lab = ct.la + ct.lb; d.L = ct.la + ct.lb + ct.lc;
+  d.bra_pure = ct.bra_pure;
+  d.ncA = ct.ncA; d.ncB = ct.ncB; d.ncc = ct.ncc;
+  d.nA = ct.nA; d.nB = ct.nB; d.nC = ct.nC; d.nblk = d.nA * d.nB * d.nC;
+  d.orient = orient;
+  d.onA = orient ? ct.nB : ct.nA;
+  d.onB = orient ? ct.nA : ct.nB;
+  d.Kab = kmax; d.Kc = Kc; d.K = kmax * Kc;
+  d.Kab_rec = Kab_rec;
+  d.NV = ct.NV; d.NW = ct.NW; d.NF = ct.NF; d.NACC = ct.NACC;
+  for (int e = 0; e <= d.Lab; ++e) d.vlev_start[e] = ct.vlev_start[e];
+  d.nW = ct.NW;
+  d.ngt = ct.nkrow * ct.ncc;
+  d.nkrow = ct.nkrow;
+  for (int j = 0; j <= ct.lb; ++j) d.hrows[j] = ct.hrows[j];
+  for (int j = 0; j <= ct.lb + 1; ++j) d.hstart[j] = ct.hstart[j];
+  d.nbA = ct.nbA; d.nbB = ct.nbB;
+  d.vtab = dc.vtab; d.wtab = dc.wtab; d.atab = dc.atab; d.gptr = dc.gptr; d.gterm = dc.gterm;
+  d.gdst = dc.gdst; d.pal = dc.pal; d.kptr = dc.kptr; d.kent = dc.kent; d.htab = dc.htab;
+  d.baptr = dc.baptr; d.baent = dc.baent; d.bbptr = dc.bbptr; d.bbent = dc.bbent;
+  d.boys_tab = ds->boys_tab; d.boys_mid = ds->boys_mid; d.boys_cL = boys_large_const(d.L);
+  fill_layout(d, ct, sh);
+  d.nchunk = (d.K + d.G - 1) / d.G;
+  return sh.smem_bytes;
+}
+
+}  // namespace lx3c
+
+namespace lx3c {
+
+// Orientation.  HRR (Eq. hrr) builds the target centre's quanta from the
+// recurrence centre's through AB; when the target is compact and the
+// recurrence centre diffuse, P sits near the target and the transfer
+// cancels, amplifying FP64 rounding by about
+//   amp = ((|AB| + s) / (|P - target| + s))^l_target,  s = 1/sqrt(2 gamma),
+// weighted by the primitive pair's share of the largest prefactor
+// |c_a c_b exp(-za zb/gamma AB^2)/gamma| in the pair.  A pair keeps one
+// orientation (the one with the smaller worst weighted amp) when that worst
+// amp is at most kAmpMax; otherwise every primitive pair runs on its more
+// compact centre (two launches, the second accumulating transposed).
+// Without HRR (lb = 0) the caller's orientation is always kept.
+void split_orientation(const lx3c_basis* orb, int a, int b, int la, int lb, std::vector<int>& primA,
+                       std::vector<int>& primB) {
+  const double kAmpMax = 300.0;
+  const int Ka = orb->k[a], Kb = orb->k[b];
+  const double* A = &orb->xyz[3 * a];
+  const double* B = &orb->xyz[3 * b];
+  double ab2 = 0;
+  for (int x = 0; x < 3; ++x) ab2 += (A[x] - B[x]) * (A[x] - B[x]);
+  const double dab = std::sqrt(ab2);
+  std::vector<double> wgt(Ka * Kb), ampA(Ka * Kb), ampB(Ka * Kb);
+  double wmax = 0;
+  for (int ia = 0; ia < Ka; ++ia)
+    for (int ib = 0; ib < Kb; ++ib) {
+      double za = orb->exps[orb->off[a] + ia], zb = orb->exps[orb->off[b] + ib], g = za + zb;
+      double w = std::fabs(orb->coefs[orb->off[a] + ia] * orb->coefs[orb->off[b] + ib]) *
+                 std::exp(-za * zb / g * ab2) / g;
+      double sg = 1.0 / std::sqrt(2.0 * g);
+      ampA[ia * Kb + ib] = std::pow((dab + sg) / (za / g * dab + sg), lb);
+      ampB[ia * Kb + ib] = std::pow((dab + sg) / (zb / g * dab + sg), la);
+      wgt[ia * Kb + ib] = w;
+      wmax = std::max(wmax, w);
+    }
+  double worstA = 0, worstB = 0;
+  for (int r = 0; r < Ka * Kb; ++r) {
+    double f = wmax > 0 ? wgt[r] / wmax : 1.0;
+    worstA = std::max(worstA, ampA[r] * f);
+    worstB = std::max(worstB, ampB[r] * f);
+  }
+  for (int ia = 0; ia < Ka; ++ia)
+    for (int ib = 0; ib < Kb; ++ib) {
+      bool onB;
+      if (lb == 0) onB = false;
+      else if (std::min(worstA, worstB) <= kAmpMax) onB = worstB < worstA;
+      else onB = orb->exps[orb->off[b] + ib] > orb->exps[orb->off[a] + ia];
+      (onB ? primB : primA).push_back(ia * Kb + ib);
+    }
+}
+
+}  // namespace lx3c
 
 // One kernel launch of a plan: one orientation of the pair list.
 struct Launch {
@@ -295,34 +362,10 @@ lx3c_status make_launch(DevState* ds, lx3c_plan* p, int orient, const std::vecto
   DevClass* dc;
   lx3c_status rc = device_class(ds, *ct, &dc);
   if (rc) return rc;
-  LaunchShape sh = choose_shape(*ct, kmax, p->Kc, p->naux, ds->smem_per_sm);
-  if (sh.smem_bytes < 0 || sh.smem_bytes > 232448)
-    return fail(LX3C_ENOTSUP, "eri3c_plan: class does not fit in shared memory");
   ClassDesc& d = L.desc;
-  std::memset(&d, 0, sizeof(d));
-  d.la = l1; d.lb = l2; d.lc = p->lc; d.Lab = l1 + l2; d.L = l1 + l2 + p->lc; d.bra_pure = p->bra_pure;
-  d.ncA = ct->ncA; d.ncB = ct->ncB; d.ncc = ct->ncc;
-  d.nA = ct->nA; d.nB = ct->nB; d.nC = ct->nC; d.nblk = d.nA * d.nB * d.nC;
-  d.orient = orient;
-  d.onA = orient ? ct->nB : ct->nA;
-  d.onB = orient ? ct->nA : ct->nB;
-  d.Kab = kmax; d.Kc = p->Kc; d.K = kmax * p->Kc;
-  d.Kab_rec = p->Ka * p->Kb;
-  d.NV = ct->NV; d.NW = ct->NW; d.NF = ct->NF; d.NACC = ct->NACC;
-  for (int e = 0; e <= d.Lab; ++e) d.vlev_start[e] = ct->vlev_start[e];
-  d.nW = ct->NW;
-  d.ngt = ct->nkrow * ct->ncc;
-  d.nkrow = ct->nkrow;
-  for (int j = 0; j <= l2; ++j) d.hrows[j] = ct->hrows[j];
-  for (int j = 0; j <= l2 + 1; ++j) d.hstart[j] = ct->hstart[j];
-  d.nbA = ct->nbA; d.nbB = ct->nbB;
-  d.vtab = dc->vtab; d.wtab = dc->wtab; d.atab = dc->atab; d.gptr = dc->gptr; d.gterm = dc->gterm;
-  d.gdst = dc->gdst; d.pal = dc->pal; d.kptr = dc->kptr; d.kent = dc->kent; d.htab = dc->htab;
-  d.baptr = dc->baptr; d.baent = dc->baent; d.bbptr = dc->bbptr; d.bbent = dc->bbent;
-  d.boys_tab = ds->boys_tab; d.boys_mid = ds->boys_mid; d.boys_cL = boys_large_const(d.L);
+  if (fill_class_desc(d, *ct, *dc, ds, orient, kmax, p->Ka * p->Kb, p->Kc, p->naux) < 0)
+    return fail(LX3C_ENOTSUP, "eri3c_plan: class does not fit in shared memory");
   d.npair = p->npair; d.naux = p->naux;
-  fill_layout(d, *ct, sh);
-  d.nchunk = (d.K + d.G - 1) / d.G;
   d.ntile_aux = (int)((p->naux + d.T - 1) / d.T);
   d.nsub = L.nsub;
   d.ntiles = L.nsub * d.ntile_aux;
@@ -378,58 +421,12 @@ lx3c_status lx3c_eri3c_plan(lx3c_plan** out, const lx3c_basis* orb, const lx3c_b
     const ClassTables& ct = class_tables(la, lb, lc, p->bra_pure);
     p->nblk = (int64_t)ct.nA * ct.nB * ct.nC;
   }
-  // Orientation.  HRR (Eq. hrr) builds the target centre's quanta from the
-  // recurrence centre's through AB; when the target is compact and the
-  // recurrence centre diffuse, P sits near the target and the transfer
-  // cancels, amplifying FP64 rounding by about
-  //   amp = ((|AB| + s) / (|P - target| + s))^l_target,  s = 1/sqrt(2 gamma),
-  // weighted by the primitive pair's share of the largest prefactor
-  // |c_a c_b exp(-za zb/gamma AB^2)/gamma| in the pair.  A pair keeps one
-  // orientation (the one with the smaller worst weighted amp) when that worst
-  // amp is below kAmpMax; otherwise every primitive pair runs on its more
-  // compact centre (two launches, the second accumulating transposed).
-  // Without HRR (lb = 0) the caller's orientation is always kept.
-  const double kAmpMax = 300.0;
   std::vector<int4> subA, subB;
   std::vector<int> primA, primB;
   int kA = 0, kB = 0;
-  std::vector<double> wgt(Ka * Kb), ampA(Ka * Kb), ampB(Ka * Kb);
   for (int64_t i = 0; i < npair; ++i) {
-    int32_t a = pairs[2 * i], b = pairs[2 * i + 1];
-    const double* A = &orb->xyz[3 * a];
-    const double* B = &orb->xyz[3 * b];
-    double ab2 = 0;
-    for (int x = 0; x < 3; ++x) ab2 += (A[x] - B[x]) * (A[x] - B[x]);
-    const double dab = std::sqrt(ab2);
-    double wmax = 0;
-    for (int ia = 0; ia < Ka; ++ia)
-      for (int ib = 0; ib < Kb; ++ib) {
-        double za = orb->exps[orb->off[a] + ia], zb = orb->exps[orb->off[b] + ib], g = za + zb;
-        double w = std::fabs(orb->coefs[orb->off[a] + ia] * orb->coefs[orb->off[b] + ib]) *
-                   std::exp(-za * zb / g * ab2) / g;
-        double sg = 1.0 / std::sqrt(2.0 * g);
-        // recurrences on A: quanta moved to B (distance |P-B| = za/g |AB|); on B: to A
-        ampA[ia * Kb + ib] = std::pow((dab + sg) / (za / g * dab + sg), lb);
-        ampB[ia * Kb + ib] = std::pow((dab + sg) / (zb / g * dab + sg), la);
-        wgt[ia * Kb + ib] = w;
-        wmax = std::max(wmax, w);
-      }
-    double worstA = 0, worstB = 0;
-    for (int r = 0; r < Ka * Kb; ++r) {
-      double f = wmax > 0 ? wgt[r] / wmax : 1.0;
-      worstA = std::max(worstA, ampA[r] * f);
-      worstB = std::max(worstB, ampB[r] * f);
-    }
     int oa = (int)primA.size(), ob = (int)primB.size();
-    for (int ia = 0; ia < Ka; ++ia)
-      for (int ib = 0; ib < Kb; ++ib) {
-        const int r = ia * Kb + ib;
-        bool onB;
-        if (lb == 0) onB = false;
-        else if (std::min(worstA, worstB) <= kAmpMax) onB = worstB < worstA;
-        else onB = orb->exps[orb->off[b] + ib] > orb->exps[orb->off[a] + ia];
-        (onB ? primB : primA).push_back(r);
-      }
+    split_orientation(orb, pairs[2 * i], pairs[2 * i + 1], la, lb, primA, primB);
     int na = (int)primA.size() - oa, nb = (int)primB.size() - ob;
     if (na) subA.push_back(int4{(int)i, oa, na, 0});
     if (nb) subB.push_back(int4{(int)i, ob, nb, na > 0 ? 1 : 0});

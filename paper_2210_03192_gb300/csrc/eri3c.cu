@@ -212,9 +212,18 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
   const int auxsz = 3 + kAuxRec * d.Kc;
 
   for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
-    const long long sub = tile / d.ntile_aux;
-    const int aux0 = (int)(tile - sub * d.ntile_aux) * T;
-    const int tv = (int)min((long long)T, d.naux - aux0);
+    long long sub;
+    int aux0, tv;
+    if (d.tiles) {
+      const int4 tt = __ldg(d.tiles + tile);
+      sub = tt.x;
+      aux0 = tt.y;
+      tv = tt.z;
+    } else {
+      sub = tile / d.ntile_aux;
+      aux0 = (int)(tile - sub * d.ntile_aux) * T;
+      tv = (int)min((long long)T, d.naux - aux0);
+    }
     const int4 sp = __ldg(d.subpairs + sub);
     const long long pair = sp.x;
     const int kab = sp.z, accum = sp.w;
@@ -514,6 +523,53 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
       }
       __syncthreads();
       cur = d.BB;
+    }
+    if (d.digest) {
+      // ---- DF-J digestion (Sec. 3): the block never leaves shared memory.
+      const int4 pao = __ldg(d.pair_ao + pair);
+      const double wg = pao.z ? 1.0 : 2.0, wj = pao.z ? 0.5 : 1.0;
+      const int nA = d.onA, nB = d.onB, nC = d.nC;
+      // gamma_P: items (t, C), each a dot product over the (A, B) block with D
+      {
+        FDiv fC;
+        fC.init(nC);
+        const unsigned n = (unsigned)(tv * nC);
+        for (unsigned w = tid; w < n; w += kThreads) {
+          const int t = (int)fC.div(w), C = (int)(w - t * nC);
+          double s = 0.0;
+          for (int A = 0; A < nA; ++A) {
+            const double* Drow = d.D + (long long)(pao.x + A) * d.ldD + pao.y;
+            for (int B = 0; B < nB; ++B) {
+              const int sidx = d.orient ? (B * nA + A) * nC + C : (A * nB + B) * nC + C;
+              s = fma(sm[BUF_T(cur, sidx, t)], __ldg(Drow + B), s);
+            }
+          }
+          atomicAdd(d.gamma + __ldg(d.aux_ao + aux0 + t) + C, wg * s);
+        }
+      }
+      // J_ab: items (A, B, group of 32 ket shells)
+      {
+        const int ng = (tv + 31) / 32;
+        FDiv fG2, fB2;
+        fG2.init(ng);
+        fB2.init(nB);
+        const unsigned n = (unsigned)(nA * nB * ng);
+        for (unsigned w = tid; w < n; w += kThreads) {
+          const int ab = (int)fG2.div(w), grp = (int)(w - ab * ng);
+          const int A = (int)fB2.div(ab), B = ab - A * nB;
+          double s = 0.0;
+          const int t1 = min(tv, grp * 32 + 32);
+          for (int t = grp * 32; t < t1; ++t) {
+            const double* cv = d.cvec + __ldg(d.aux_ao + aux0 + t);
+            for (int C = 0; C < nC; ++C) {
+              const int sidx = d.orient ? (B * nA + A) * nC + C : (A * nB + B) * nC + C;
+              s = fma(sm[BUF_T(cur, sidx, t)], __ldg(cv + C), s);
+            }
+          }
+          atomicAdd(d.J + (long long)(pao.x + A) * d.ldD + pao.y + B, wj * s);
+        }
+      }
+      continue;
     }
     // ---- store the tile's contiguous output block (transposed into the
     // caller's (A, B) order for B-oriented sub-pairs; added to the block

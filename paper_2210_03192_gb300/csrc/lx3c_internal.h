@@ -93,6 +93,21 @@ struct ClassDesc {
   const double* boys_mid;  // [kBoysNInt]
   double boys_cL;          // Gamma(L+1/2)/2 for the large-T branch
   double* out;
+  // optional explicit tile table {sub-pair, first ket-list entry, ket count, 0};
+  // when null, tiles are (sub-pair, T consecutive ket shells) over all naux
+  const int4* tiles;
+  // DF-J digestion instead of the store (Sec. 3: integral digestion callable):
+  //   gamma[aux_ao[q] + C] += w * sum_AB I[A][B][C] D[ao_a + A][ao_b + B]
+  //   J[ao_a + A][ao_b + B] += wj * sum_{q,C} I[A][B][C] c[aux_ao[q] + C]
+  // w = 2 (1 for a == b), wj = 1 (1/2 for a == b); J is symmetrised afterwards.
+  int digest;
+  long long ldD;           // row stride of D and J
+  const double* D;
+  const double* cvec;
+  double* gamma;
+  double* J;
+  const int4* pair_ao;     // per pair: {ao_a, ao_b, a == b, 0}
+  const int* aux_ao;       // per ket-list entry: first AO
 };
 
 // Device view of a basis (shell tables in HBM).
@@ -132,6 +147,38 @@ struct ClassTables {
   std::vector<int4> acc_key;
 };
 
+// Device-side constant tables (capi.cu)
+struct DevClass {
+  void* blob = nullptr;
+  const uint4* vtab;
+  const int4* wtab;
+  const unsigned* atab;
+  const int* gptr;
+  const unsigned* gterm;
+  const int* gdst;
+  const double* pal;
+  const int* kptr;
+  const int2* kent;
+  const int4* htab;
+  const int* baptr;
+  const int2* baent;
+  const int* bbptr;
+  const int2* bbent;
+};
+struct DevState;
+int device_state_get(DevState** out);                       // lx3c_status
+int device_class_get(DevState* s, const ClassTables& ct, DevClass** out);
+const double* dev_boys_tab(const DevState* s);
+const double* dev_boys_mid(const DevState* s);
+int dev_nsm(const DevState* s);
+int dev_smem(const DevState* s);
+void set_last_error(const std::string& msg);
+// Fill a launch descriptor for class (l1 l2|lc) (orientation `orient` of the
+// caller's (la, lb)), kmax primitive pairs per sub-pair; returns smem bytes or
+// -1 if the class does not fit.
+int fill_class_desc(ClassDesc& d, const ClassTables& ct, const DevClass& dc, const DevState* ds, int orient,
+                    int kmax, int Kab_rec, int Kc, long long naux_for_shape);
+
 // planner entry points (plan.cu)
 const ClassTables& class_tables(int la, int lb, int lc, int bra_pure);
 std::vector<double> solid_matrix(int l);   // [(m+l)*ncart(l) + c]
@@ -150,4 +197,25 @@ struct LaunchShape {
 LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit);
 void fill_layout(ClassDesc& d, const ClassTables& ct, const LaunchShape& s);
 
+// Orientation split of one pair's primitive pairs (capi.cu).
+}  // namespace lx3c
+
+// Shell table, host copy plus device SoA copy (opaque in the C ABI).
+struct lx3c_basis {
+  int64_t nshell = 0, nprim = 0;
+  std::vector<int32_t> l, k, atom;
+  std::vector<int64_t> off;
+  std::vector<double> xyz, exps, coefs;
+  int32_t* d_l = nullptr;
+  int32_t* d_k = nullptr;
+  int64_t* d_off = nullptr;
+  double* d_xyz = nullptr;
+  double* d_exps = nullptr;
+  double* d_coefs = nullptr;
+  lx3c::DevBasis dev() const { return lx3c::DevBasis{d_l, d_k, d_off, d_xyz, d_exps, d_coefs}; }
+};
+
+namespace lx3c {
+void split_orientation(const lx3c_basis* orb, int a, int b, int la, int lb, std::vector<int>& primA,
+                       std::vector<int>& primB);
 }  // namespace lx3c
