@@ -165,6 +165,8 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  * shell order, components m = -l..l), for every ket shell P of the aux basis.
  *
  * lx3c_dfj_plan: setup (synchronises `stream`, not part of the timed path).
+ *   flags bit 0: also prepare the nuclear gradient (lx3c_dfj_grad); needs an
+ *   atom index on every shell and orbital shells with l < LX3C_LMAX_ORB.
  *   Screening: a (pair, ket) triple is kept when Q_ab Q_P >= schwarz_tol, with
  *   Q_ab = sum over primitive pairs of |c_a c_b| exp(-za zb/g AB^2)
  *   sqrt(2 pi^{5/2}/(g^2 sqrt(2g))) (|PA|^2+1/(2g))^{la/2} (|PB|^2+1/(2g))^{lb/2}
@@ -173,11 +175,20 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  *   Returns LX3C_ENOTSUP for orbital shells above LX3C_LMAX_ORB.
  * lx3c_dfj_execute: D (device, nao x nao row-major, symmetric), c (device,
  *   naux_ao) in; gamma (device, naux_ao) and J (device, nao x nao, symmetric)
- *   overwritten.  Asynchronous on `stream`.  Summation order inside gamma and J
- *   follows FP64 atomic arrival order.
- * lx3c_dfj_info: out[0..6] = groups, screened (pair, ket shell) triples,
+ *   overwritten; either output may be NULL to skip it (not both).
+ *   Asynchronous on `stream`.  Summation order inside gamma and J follows FP64
+ *   atomic arrival order.
+ * lx3c_dfj_energy: gamma as above (J skipped) and *energy = c^T gamma
+ *   (device scalar), the DF-J energy whose gradient lx3c_dfj_grad returns.
+ * lx3c_dfj_info: out[0..9] = groups, screened (pair, ket shell) triples,
  *   integrals digested, algorithmic FP64 flops per execute, kernel launches
- *   per execute, nao, naux_ao.
+ *   per execute, nao, naux_ao, natom, gradient FP64 flops, gradient launches.
+ * lx3c_dfj_grad: dE/dR for E = c^T gamma with D and c held fixed (not in the
+ *   paper): for every screened triple the derivative integrals
+ *   d/dA (ab|P) = sum_prim [2 za (a+1 b|P) - a (a-1 b|P)] (same for B) are
+ *   formed on the fly in Cartesian-bra classes and contracted with
+ *   W = w D_ab c_P; dE/dC = -(dE/dA + dE/dB) (translational invariance).
+ *   grad (device, natom x 3) overwritten; accumulated with FP64 atomics.
  * lx3c_dfj_group: the screened task list of class group gi (for checks):
  *   info[8] = {la, lb, lc, ka, kb, kc, npair, nket}; pairs[2*npair] shell
  *   indices (a, b); counts[npair]: pair i is kept with the first counts[i]
@@ -185,9 +196,12 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  *   pointer may be NULL.
  */
 lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basis* aux, double schwarz_tol,
-                          void* stream);
+                          int flags, void* stream);
 lx3c_status lx3c_dfj_execute(lx3c_dfj* plan, const double* D, const double* c, double* gamma, double* J,
                              void* stream);
+lx3c_status lx3c_dfj_energy(lx3c_dfj* plan, const double* D, const double* c, double* gamma, double* energy,
+                            void* stream);
+lx3c_status lx3c_dfj_grad(lx3c_dfj* plan, const double* D, const double* c, double* grad, void* stream);
 lx3c_status lx3c_dfj_info(const lx3c_dfj* plan, double* out, int n);
 lx3c_status lx3c_dfj_group(const lx3c_dfj* plan, int gi, int32_t* info, int32_t* pairs, int32_t* counts,
                            int32_t* auxs);

@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import LibraryError, check, ptr
 from . import workloads  # noqa: F401  (seeded input generators)
 
-__all__ = ["DeviceBasis", "Eri3cPlan", "DFJPlan", "eri3c", "eri3c_host", "boys", "class_flops", "solid_harmonics",
+__all__ = ["DeviceBasis", "Eri3cPlan", "DFJPlan", "DFJEnergy", "eri3c", "eri3c_host", "boys", "class_flops", "solid_harmonics",
            "cvrr2_expansion", "LibraryError", "workloads"]
 
 
@@ -147,17 +147,37 @@ def eri3c_host(orb, aux, pairs, auxs, bra_pure=True, out=None, stream=None):
 class DFJPlan:
     """Screened DF-J build (lx3c_dfj): gamma_P and J_mn from D and c, Sec. 3."""
 
-    def __init__(self, orb, aux, schwarz_tol=1e-12, stream=None):
+    def __init__(self, orb, aux, schwarz_tol=1e-12, gradient=False, stream=None):
         L = _lib.load()
         self.orb = orb if isinstance(orb, DeviceBasis) else DeviceBasis(orb, stream)
         self.aux = aux if isinstance(aux, DeviceBasis) else DeviceBasis(aux, stream)
         self.handle = ctypes.c_void_p()
         check(L.lx3c_dfj_plan(ctypes.byref(self.handle), self.orb.handle, self.aux.handle, float(schwarz_tol),
-                              _stream_handle(stream)), "lx3c_dfj_plan")
-        info = np.zeros(7)
-        check(L.lx3c_dfj_info(self.handle, ptr(info), 7), "lx3c_dfj_info")
+                              1 if gradient else 0, _stream_handle(stream)), "lx3c_dfj_plan")
+        info = np.zeros(10)
+        check(L.lx3c_dfj_info(self.handle, ptr(info), 10), "lx3c_dfj_info")
         self.ngroups, self.ntasks, self.nint, self.flops, self.launches, self.nao, self.naux_ao = (
             int(info[0]), int(info[1]), float(info[2]), float(info[3]), int(info[4]), int(info[5]), int(info[6]))
+        self.natom, self.grad_flops, self.grad_launches = int(info[7]), float(info[8]), int(info[9])
+
+    def energy(self, D, c, stream=None):
+        """E = c^T gamma (device scalar tensor) and gamma."""
+        torch = _torch()
+        gamma = torch.empty(self.naux_ao, dtype=torch.float64, device=D.device)
+        E = torch.empty((), dtype=torch.float64, device=D.device)
+        check(_lib.load().lx3c_dfj_energy(self.handle, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                          ctypes.c_void_p(gamma.data_ptr()), ctypes.c_void_p(E.data_ptr()),
+                                          _stream_handle(stream)), "lx3c_dfj_energy")
+        return E, gamma
+
+    def gradient(self, D, c, grad=None, stream=None):
+        """dE/dR [natom, 3] for E = c^T gamma (D, c fixed)."""
+        torch = _torch()
+        if grad is None:
+            grad = torch.empty((self.natom, 3), dtype=torch.float64, device=D.device)
+        check(_lib.load().lx3c_dfj_grad(self.handle, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                        ctypes.c_void_p(grad.data_ptr()), _stream_handle(stream)), "lx3c_dfj_grad")
+        return grad
 
     def execute(self, D, c, gamma=None, J=None, stream=None):
         torch = _torch()
@@ -203,6 +223,55 @@ class DFJPlan:
         if h is not None and h.value and _lib._lib is not None:
             _lib._lib.lx3c_dfj_destroy(h)
             self.handle = None
+
+
+def _moved(basis, R):
+    """Copy of a shell table with every shell centred on its atom's row of R."""
+    from .workloads import Basis
+    b = Basis(basis.l, basis.k, basis.off, np.asarray(R)[np.asarray(basis.atom)], basis.exps, basis.coefs,
+              basis.atom)
+    return b
+
+
+class DFJEnergy:
+    """E(R) = c^T gamma(R) as a torch.autograd.Function (not in the paper).
+
+    E = DFJEnergy.apply(R, orb, aux, D, c[, tol]) with R [natom, 3] float64
+    atom positions (bohr); shells sit on R[atom].  Forward: lx3c_dfj_energy.
+    Backward: lx3c_dfj_grad (adjoint derivative integrals contracted with
+    D_ab c_P on the fly), dE/dR [natom, 3].  D and c are held fixed.
+    """
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, R, orb, aux, D, c, tol=1e-12):
+                Rn = R.detach().cpu().numpy()
+                plan = DFJPlan(_moved(orb, Rn), _moved(aux, Rn), tol, gradient=True)
+                E, _ = plan.energy(D, c)
+                ctx.plan = plan
+                ctx.save_for_backward(D, c)
+                ctx.rdev = R.device
+                return E.to(R.device)
+
+            @staticmethod
+            def backward(ctx, gE):
+                D, c = ctx.saved_tensors
+                g = ctx.plan.gradient(D, c)
+                return (gE.to(g.device) * g).to(ctx.rdev), None, None, None, None, None
+
+        return _F
+
+    _cls = None
+
+    @classmethod
+    def apply(cls, *args):
+        if cls._cls is None:
+            cls._cls = cls._fn()
+        return cls._cls.apply(*args)
 
 
 def boys(T, mmax, stream=None):

@@ -43,7 +43,9 @@ EXPORTS = {
     "lx3c_eri3c_noalloc": (ctypes.c_int, [ctypes.c_int] * 7 + [ctypes.c_void_p] * 9 + [ctypes.c_int64,
                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lx3c_dfj_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p,
-                                     ctypes.c_double, ctypes.c_void_p]),
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    "lx3c_dfj_grad": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "lx3c_dfj_energy": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "lx3c_dfj_execute": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "lx3c_dfj_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lx3c_dfj_group": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -27,7 +28,7 @@
 
 namespace lx3c {
 cudaError_t launch_pair_precompute(const DevBasis& orb, const int32_t* pairs, long long npair, int Ka, int Kb,
-                                   double* rec, double* ab, cudaStream_t st);
+                                   double* rec, double* ab, cudaStream_t st, int scale_a = 0, int scale_b = 0);
 cudaError_t launch_aux_precompute(const DevBasis& aux, const int32_t* auxs, long long naux, int Kc, double* rec,
                                   double* cxyz, cudaStream_t st);
 cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st);
@@ -62,6 +63,20 @@ __global__ void symmetrize(double* J, long long n) {
     J[i * n + j] = s;
     J[j * n + i] = s;
   }
+}
+
+// energy = sum_i c_i gamma_i (one block, fixed-order tree reduction)
+__global__ void dot_energy(const double* __restrict__ c, const double* __restrict__ g, long long n, double* out) {
+  __shared__ double part[256];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += 256) s = fma(c[i], g[i], s);
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = part[0];
 }
 
 constexpr double kPi = 3.14159265358979323846;
@@ -124,7 +139,58 @@ struct DfjGroup {
   double* d_auxrec = nullptr;
   double* d_auxc = nullptr;
   DfjLaunch L[2];
+  // gradient: derivative classes (centre 0: (la+1,lb) scaled, (la-1,lb);
+  // centre 1: (la,lb+1) scaled, (la,lb-1)), each with two orientations
+  struct Deriv {
+    int centre, plus, l1, l2;
+    DfjLaunch L[2];
+    int4* d_gmap = nullptr;
+  };
+  std::vector<Deriv> deriv;
+  int2* d_pair_atoms = nullptr;
+  int* d_aux_atom = nullptr;
+  double gflops = 0;
 };
+
+// Derivative map for one derivative class (see ClassDesc::gmap).
+std::vector<int4> derivative_map(int la, int lb, int centre, int plus, int gstart[4], int& nmax) {
+  std::vector<std::vector<int4>> byax(3);
+  const int l1 = la + (centre == 0 ? (plus ? 1 : -1) : 0), l2 = lb + (centre == 1 ? (plus ? 1 : -1) : 0);
+  const int ncB = ncart(lb);
+  auto carts = [](int l) {
+    std::vector<std::array<int, 3>> v;
+    for (int x = l; x >= 0; --x)
+      for (int y = l - x; y >= 0; --y) v.push_back({x, y, l - x - y});
+    return v;
+  };
+  auto c1 = carts(l1), c2 = carts(l2);
+  for (size_t i1 = 0; i1 < c1.size(); ++i1)
+    for (size_t i2 = 0; i2 < c2.size(); ++i2)
+      for (int ax = 0; ax < 3; ++ax) {
+        std::array<int, 3> a = c1[i1], b = c2[i2];
+        std::array<int, 3>& moved = centre == 0 ? a : b;
+        int factor;
+        if (plus) {  // (x + 1_ax) present in the block: original x = moved - 1_ax
+          if (moved[ax] < 1) continue;
+          moved[ax] -= 1;
+          factor = 1;
+        } else {     // (x - 1_ax) in the block: original x = moved + 1_ax, factor -x_ax
+          moved[ax] += 1;
+          factor = -moved[ax];
+        }
+        const int ia = cart_index(a[0], a[1], a[2]), ib = cart_index(b[0], b[1], b[2]);
+        byax[ax].push_back(int4{(int)i1, (int)i2, ia * ncB + ib, factor});
+      }
+  std::vector<int4> out;
+  nmax = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    gstart[ax] = (int)out.size();
+    out.insert(out.end(), byax[ax].begin(), byax[ax].end());
+    nmax = std::max(nmax, (int)byax[ax].size());
+  }
+  gstart[3] = (int)out.size();
+  return out;
+}
 
 }  // namespace
 
@@ -133,7 +199,11 @@ struct lx3c_dfj {
   const lx3c_basis* aux = nullptr;
   long long nao = 0, naux_ao = 0;
   double tol = 0;
+  int natom = 0;
+  bool gradient = false;
   std::vector<DfjGroup> groups;
+  double* d_sph = nullptr;          // solid-harmonic matrices for l = 0..7
+  std::vector<int> sph_off;
 };
 
 extern "C" {
@@ -146,19 +216,35 @@ void lx3c_dfj_destroy(lx3c_dfj* p) {
     for (auto& L : g.L) {
       cudaFree(L.d_sub); cudaFree(L.d_prim); cudaFree(L.d_tiles);
     }
+    for (auto& dv : g.deriv) {
+      cudaFree(dv.d_gmap);
+      for (auto& L : dv.L) {
+        cudaFree(L.d_sub); cudaFree(L.d_prim); cudaFree(L.d_tiles);
+      }
+    }
+    cudaFree(g.d_pair_atoms); cudaFree(g.d_aux_atom);
   }
+  cudaFree(p->d_sph);
   delete p;
 }
 
 lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basis* aux, double schwarz_tol,
-                          void* stream) {
+                          int flags, void* stream) {
   if (!out) return dfail(LX3C_EINVAL, "null output pointer");
   *out = nullptr;
   if (!orb || !aux) return dfail(LX3C_EINVAL, "null basis");
   if (orb->nshell <= 0 || aux->nshell <= 0) return dfail(LX3C_EINVAL, "empty basis");
   if (!(schwarz_tol >= 0.0)) return dfail(LX3C_EINVAL, "negative or NaN tolerance");
+  const bool want_grad = (flags & 1) != 0;
   for (int64_t s = 0; s < orb->nshell; ++s)
-    if (orb->l[s] > LX3C_LMAX_ORB) return dfail(LX3C_ENOTSUP, "orbital shell beyond the supported l");
+    if (orb->l[s] > LX3C_LMAX_ORB - (want_grad ? 1 : 0))
+      return dfail(LX3C_ENOTSUP, "orbital shell beyond the supported l");
+  if (want_grad) {
+    for (int64_t s = 0; s < orb->nshell; ++s)
+      if (orb->atom[s] < 0) return dfail(LX3C_EINVAL, "gradient needs an atom index on every shell");
+    for (int64_t s = 0; s < aux->nshell; ++s)
+      if (aux->atom[s] < 0) return dfail(LX3C_EINVAL, "gradient needs an atom index on every shell");
+  }
   DevState* ds;
   int rc = device_state_get(&ds);
   if (rc) return rc;
@@ -172,6 +258,9 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
   for (int64_t s = 0; s < aux->nshell; ++s) aq[s + 1] = aq[s] + 2 * aux->l[s] + 1;
   p->nao = ao[orb->nshell];
   p->naux_ao = aq[aux->nshell];
+  p->gradient = want_grad;
+  for (int64_t s = 0; s < orb->nshell; ++s) p->natom = std::max(p->natom, orb->atom[s] + 1);
+  for (int64_t s = 0; s < aux->nshell; ++s) p->natom = std::max(p->natom, aux->atom[s] + 1);
   // ket shells by (l, K), sorted by decreasing Q_P
   std::map<std::pair<int, int>, std::vector<std::pair<double, int>>> kets;
   for (int64_t s = 0; s < aux->nshell; ++s) kets[{aux->l[s], aux->k[s]}].push_back({q_aux(aux, (int)s), (int)s});
@@ -298,6 +387,111 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
       const int occ = eri3c_occupancy(d.smem_doubles * 8);
       L.grid = (int)std::min<long long>(L.ntiles, (long long)dev_nsm(ds) * occ * 8);
     }
+    if (!want_grad) continue;
+    // ---- gradient launches
+    std::vector<int2> pat(np);
+    std::vector<int> aat(na);
+    for (long long i = 0; i < np; ++i) pat[i] = int2{orb->atom[g.pairs[2 * i]], orb->atom[g.pairs[2 * i + 1]]};
+    for (long long q = 0; q < na; ++q) aat[q] = aux->atom[g.auxs[q]];
+    DCUDA(cudaMalloc(&g.d_pair_atoms, np * sizeof(int2)));
+    DCUDA(cudaMalloc(&g.d_aux_atom, na * 4));
+    DCUDA(cudaMemcpyAsync(g.d_pair_atoms, pat.data(), np * sizeof(int2), cudaMemcpyHostToDevice, st));
+    DCUDA(cudaMemcpyAsync(g.d_aux_atom, aat.data(), na * 4, cudaMemcpyHostToDevice, st));
+    for (int centre = 0; centre < 2; ++centre)
+      for (int plus = 1; plus >= 0; --plus) {
+        const int l1 = g.la + (centre == 0 ? (plus ? 1 : -1) : 0), l2 = g.lb + (centre == 1 ? (plus ? 1 : -1) : 0);
+        if (l1 < 0 || l2 < 0) continue;
+        DfjGroup::Deriv dv;
+        dv.centre = centre; dv.plus = plus; dv.l1 = l1; dv.l2 = l2;
+        int gst[4], nmax = 0;
+        std::vector<int4> gmap = derivative_map(g.la, g.lb, centre, plus, gst, nmax);
+        DCUDA(cudaMalloc(&dv.d_gmap, gmap.size() * sizeof(int4)));
+        DCUDA(cudaMemcpyAsync(dv.d_gmap, gmap.data(), gmap.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+        std::vector<int4> dsub[2];
+        std::vector<int> dprim[2];
+        int dk[2] = {0, 0};
+        for (long long i = 0; i < np; ++i) {
+          int oa = (int)dprim[0].size(), ob = (int)dprim[1].size();
+          split_orientation(orb, g.pairs[2 * i], g.pairs[2 * i + 1], l1, l2, dprim[0], dprim[1]);
+          int na_ = (int)dprim[0].size() - oa, nb_ = (int)dprim[1].size() - ob;
+          if (na_) dsub[0].push_back(int4{(int)i, oa, na_, 0});
+          if (nb_) dsub[1].push_back(int4{(int)i, ob, nb_, 0});
+          dk[0] = std::max(dk[0], na_);
+          dk[1] = std::max(dk[1], nb_);
+        }
+        for (int o = 0; o < 2; ++o) {
+          if (dsub[o].empty()) continue;
+          DfjLaunch& L = dv.L[o];
+          const ClassTables* ct;
+          try {
+            ct = &class_tables(o ? l2 : l1, o ? l1 : l2, g.lc, 0);
+          } catch (std::exception& e) {
+            return dfail(LX3C_ENOTSUP, e.what());
+          }
+          DevClass* dc;
+          rc = device_class_get(ds, *ct, &dc);
+          if (rc) return rc;
+          ClassDesc& d = L.desc;
+          if (fill_class_desc(d, *ct, *dc, ds, o, dk[o], Kab, g.Kc, cmax) < 0)
+            return dfail(LX3C_ENOTSUP, "derivative class does not fit in shared memory");
+          const int nch = std::max(1, (nmax + 31) / 32);
+          const int nAp = 2 * g.la + 1, ncA = ncart(g.la), nBp = 2 * g.lb + 1, ncB = ncart(g.lb);
+          d.g_base = d.smem_doubles;
+          d.smem_doubles += nAp * ncB + ncA * ncB + d.T * 3 * nch;
+          if (d.smem_doubles * 8 > 232448) return dfail(LX3C_ENOTSUP, "gradient epilogue does not fit");
+          d.g_centre = centre;
+          d.g_nAp = nAp; d.g_ncA = ncA; d.g_nBp = nBp; d.g_ncB = ncB; d.g_nch = nch;
+          for (int k = 0; k < 4; ++k) d.gstart[k] = gst[k];
+          d.gmap = dv.d_gmap;
+          std::vector<int4> tiles;
+          for (size_t s2 = 0; s2 < dsub[o].size(); ++s2) {
+            const int cnt = g.counts[dsub[o][s2].x];
+            for (int a0 = 0; a0 < cnt; a0 += d.T) tiles.push_back(int4{(int)s2, a0, std::min(d.T, cnt - a0), 0});
+          }
+          L.ntiles = (long long)tiles.size();
+          DCUDA(cudaMalloc(&L.d_sub, dsub[o].size() * sizeof(int4)));
+          DCUDA(cudaMalloc(&L.d_prim, std::max<size_t>(dprim[o].size(), 1) * sizeof(int)));
+          DCUDA(cudaMalloc(&L.d_tiles, tiles.size() * sizeof(int4)));
+          DCUDA(cudaMemcpyAsync(L.d_sub, dsub[o].data(), dsub[o].size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+          DCUDA(cudaMemcpyAsync(L.d_prim, dprim[o].data(), dprim[o].size() * sizeof(int), cudaMemcpyHostToDevice, st));
+          DCUDA(cudaMemcpyAsync(L.d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+          d.npair = np; d.naux = na;
+          d.nsub = (long long)dsub[o].size();
+          d.ntiles = L.ntiles;
+          d.ntile_aux = 1;
+          d.tiles = L.d_tiles; d.subpairs = L.d_sub; d.primidx = L.d_prim;
+          d.pairrec = g.d_pairrec; d.pairab = g.d_pairab; d.auxrec = g.d_auxrec; d.auxc = g.d_auxc;
+          d.digest = 2;
+          d.ldD = p->nao;
+          d.pair_ao = g.d_pair_ao; d.aux_ao = g.d_aux_ao;
+          d.pair_atoms = g.d_pair_atoms; d.aux_atom = g.d_aux_atom;
+          const int occ = eri3c_occupancy(d.smem_doubles * 8);
+          L.grid = (int)std::min<long long>(L.ntiles, (long long)dev_nsm(ds) * occ * 8);
+        }
+        double fl = 0;
+        lx3c_class_flops(l1, l2, g.lc, Kab, g.Kc, 0, &fl);
+        g.gflops += (fl + 2.0 * gmap.size() * (2 * g.lc + 1)) * (double)g.ntasks;
+        g.deriv.push_back(dv);
+      }
+  }
+  if (want_grad) {
+    std::vector<double> sph;
+    p->sph_off.assign(9, 0);
+    for (int l = 0; l <= 7; ++l) {
+      auto T = solid_matrix(l);
+      p->sph_off[l] = (int)sph.size();
+      sph.insert(sph.end(), T.begin(), T.end());
+    }
+    p->sph_off[8] = (int)sph.size();
+    DCUDA(cudaMalloc(&p->d_sph, sph.size() * 8));
+    DCUDA(cudaMemcpyAsync(p->d_sph, sph.data(), sph.size() * 8, cudaMemcpyHostToDevice, st));
+    DCUDA(cudaStreamSynchronize(st));
+    for (auto& g : p->groups)
+      for (auto& dv : g.deriv)
+        for (auto& L : dv.L) {
+          L.desc.Ta = p->d_sph + p->sph_off[g.la];
+          L.desc.Tb = p->d_sph + p->sph_off[g.lb];
+        }
   }
   DCUDA(cudaStreamSynchronize(st));
   *out = p.release();
@@ -306,10 +500,10 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
 
 lx3c_status lx3c_dfj_execute(lx3c_dfj* p, const double* D, const double* c, double* gamma, double* J, void* stream) {
   if (!p) return dfail(LX3C_EINVAL, "null plan");
-  if (!D || !c || !gamma || !J) return dfail(LX3C_EINVAL, "null pointer");
+  if (!D || !c || (!gamma && !J)) return dfail(LX3C_EINVAL, "null pointer");
   cudaStream_t st = (cudaStream_t)stream;
-  DCUDA(cudaMemsetAsync(gamma, 0, p->naux_ao * 8, st));
-  DCUDA(cudaMemsetAsync(J, 0, p->nao * p->nao * 8, st));
+  if (gamma) DCUDA(cudaMemsetAsync(gamma, 0, p->naux_ao * 8, st));
+  if (J) DCUDA(cudaMemsetAsync(J, 0, p->nao * p->nao * 8, st));
   for (auto& g : p->groups) {
     const long long np = (long long)g.counts.size(), na = (long long)g.auxs.size();
     DCUDA(launch_pair_precompute(p->orb->dev(), g.d_pairs, np, g.Ka, g.Kb, g.d_pairrec, g.d_pairab, st));
@@ -324,23 +518,64 @@ lx3c_status lx3c_dfj_execute(lx3c_dfj* p, const double* D, const double* c, doub
       DCUDA(launch_eri3c(d, L.grid, st));
     }
   }
-  dim3 blk(32, 8), grd((unsigned)((p->nao + 31) / 32), (unsigned)((p->nao + 7) / 8));
-  symmetrize<<<grd, blk, 0, st>>>(J, p->nao);
+  if (J) {
+    dim3 blk(32, 8), grd((unsigned)((p->nao + 31) / 32), (unsigned)((p->nao + 7) / 8));
+    symmetrize<<<grd, blk, 0, st>>>(J, p->nao);
+    DCUDA(cudaGetLastError());
+  }
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_dfj_energy(lx3c_dfj* p, const double* D, const double* c, double* gamma, double* energy,
+                            void* stream) {
+  if (!energy || !gamma) return dfail(LX3C_EINVAL, "null pointer");
+  lx3c_status rc = lx3c_dfj_execute(p, D, c, gamma, nullptr, stream);
+  if (rc) return rc;
+  dot_energy<<<1, 256, 0, (cudaStream_t)stream>>>(c, gamma, p->naux_ao, energy);
   DCUDA(cudaGetLastError());
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_dfj_grad(lx3c_dfj* p, const double* D, const double* c, double* grad, void* stream) {
+  if (!p) return dfail(LX3C_EINVAL, "null plan");
+  if (!p->gradient) return dfail(LX3C_EINVAL, "plan was built without gradient support (flags & 1)");
+  if (!D || !c || !grad) return dfail(LX3C_EINVAL, "null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  DCUDA(cudaMemsetAsync(grad, 0, (size_t)p->natom * 3 * 8, st));
+  for (auto& g : p->groups) {
+    const long long np = (long long)g.counts.size(), na = (long long)g.auxs.size();
+    DCUDA(launch_aux_precompute(p->aux->dev(), g.d_auxs, na, g.Kc, g.d_auxrec, g.d_auxc, st));
+    for (auto& dv : g.deriv) {
+      DCUDA(launch_pair_precompute(p->orb->dev(), g.d_pairs, np, g.Ka, g.Kb, g.d_pairrec, g.d_pairab, st,
+                                   dv.centre == 0 && dv.plus, dv.centre == 1 && dv.plus));
+      for (auto& L : dv.L) {
+        if (!L.ntiles) continue;
+        ClassDesc d = L.desc;
+        d.D = D;
+        d.cvec = c;
+        d.grad = grad;
+        DCUDA(launch_eri3c(d, L.grid, st));
+      }
+    }
+  }
   return LX3C_OK;
 }
 
 lx3c_status lx3c_dfj_info(const lx3c_dfj* p, double* out, int n) {
   if (!p || (!out && n > 0)) return dfail(LX3C_EINVAL, "null pointer");
-  double tasks = 0, nint = 0, flops = 0, launches = 1;
+  double tasks = 0, nint = 0, flops = 0, launches = 1, gflops = 0, glaunches = 0;
   for (auto& g : p->groups) {
     tasks += (double)g.ntasks;
     nint += g.nint;
     flops += g.flops;
+    gflops += g.gflops;
     launches += 2 + (g.L[0].ntiles > 0) + (g.L[1].ntiles > 0);
+    if (p->gradient) glaunches += 1;
+    for (auto& dv : g.deriv) glaunches += 1 + (dv.L[0].ntiles > 0) + (dv.L[1].ntiles > 0);
   }
-  const double v[] = {(double)p->groups.size(), tasks, nint, flops, launches, (double)p->nao, (double)p->naux_ao};
-  for (int i = 0; i < n && i < 7; ++i) out[i] = v[i];
+  const double v[] = {(double)p->groups.size(), tasks, nint, flops, launches, (double)p->nao, (double)p->naux_ao,
+                      (double)p->natom, gflops, glaunches};
+  for (int i = 0; i < n && i < 10; ++i) out[i] = v[i];
   return LX3C_OK;
 }
 

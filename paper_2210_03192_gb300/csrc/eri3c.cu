@@ -116,7 +116,7 @@ __device__ __forceinline__ void boys_scaled(const double* __restrict__ tab, cons
 
 // One thread per primitive pair (pair p, a-primitive ia, b-primitive ib).
 __global__ void pair_precompute(DevBasis orb, const int32_t* __restrict__ pairs, long long npair, int Ka, int Kb,
-                                double* __restrict__ rec, double* __restrict__ ab) {
+                                double* __restrict__ rec, double* __restrict__ ab, int scale_a, int scale_b) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long n = npair * Ka * Kb;
   if (i >= n) return;
@@ -135,6 +135,10 @@ __global__ void pair_precompute(DevBasis orb, const int32_t* __restrict__ pairs,
   double* o = rec + i * kPairRec;
   o[PR_G] = g;
   o[PR_K] = ca * cb * exp(-za * zb * ig * ab2) * two_pi52 * ig;
+  // derivative of a primitive: d/dA phi_a = 2 za phi_{a+1} - a phi_{a-1}; the
+  // 2 za factor of the first term rides on the coefficient
+  if (scale_a) o[PR_K] *= 2.0 * za;
+  if (scale_b) o[PR_K] *= 2.0 * zb;
   for (int x = 0; x < 3; ++x) {
     double P = (za * A[x] + zb * B[x]) * ig;
     o[PR_P + x] = P;
@@ -524,13 +528,66 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
       __syncthreads();
       cur = d.BB;
     }
+    if (d.digest == 2) {
+      // ---- gradient digestion: contract the derivative block with
+      // W = w D_ab c_P (Cartesian in the bra) without storing it.
+      const int4 pao = __ldg(d.pair_ao + pair);
+      const int2 pat = __ldg(d.pair_atoms + pair);
+      const double wp = pao.z ? 1.0 : 2.0;
+      const int nAp = d.g_nAp, ncA = d.g_ncA, nBp = d.g_nBp, ncB = d.g_ncB, nC = d.nC, nch = d.g_nch;
+      double* X = sm + d.g_base;     // [nAp][ncB]
+      double* Dc = X + nAp * ncB;    // [ncA][ncB]
+      double* part = Dc + ncA * ncB; // [tv][3][nch]
+      for (int w = tid; w < nAp * ncB; w += kThreads) {
+        const int A = w / ncB, b = w - A * ncB;
+        const double* Drow = d.D + (long long)(pao.x + A) * d.ldD + pao.y;
+        double s = 0.0;
+        for (int B = 0; B < nBp; ++B) s = fma(__ldg(Drow + B), __ldg(d.Tb + B * ncB + b), s);
+        X[w] = s;
+      }
+      __syncthreads();
+      for (int w = tid; w < ncA * ncB; w += kThreads) {
+        const int a = w / ncB, b = w - a * ncB;
+        double s = 0.0;
+        for (int A = 0; A < nAp; ++A) s = fma(__ldg(d.Ta + A * ncA + a), X[A * ncB + b], s);
+        Dc[w] = wp * s;
+      }
+      __syncthreads();
+      const int dnA = d.onA, dnB = d.onB;  // derivative class bra dims, caller order
+      for (int w = tid; w < tv * 3 * nch; w += kThreads) {
+        const int t = w / (3 * nch), rem = w - t * 3 * nch, ax = rem / nch, k = rem - ax * nch;
+        const int e0 = d.gstart[ax] + k * 32, e1 = min(d.gstart[ax + 1], e0 + 32);
+        const double* cv = d.cvec + __ldg(d.aux_ao + aux0 + t);
+        double s = 0.0;
+        for (int e = e0; e < e1; ++e) {
+          const int4 g = __ldg(d.gmap + e);
+          double tmp = 0.0;
+          for (int C = 0; C < nC; ++C) {
+            const int sidx = d.orient ? (g.y * dnA + g.x) * nC + C : (g.x * dnB + g.y) * nC + C;
+            tmp = fma(__ldg(cv + C), sm[BUF_T(cur, sidx, t)], tmp);
+          }
+          s = fma((double)g.w * Dc[g.z], tmp, s);
+        }
+        part[w] = s;
+      }
+      __syncthreads();
+      const int tatom = d.g_centre ? pat.y : pat.x;
+      for (int w = tid; w < tv * 3; w += kThreads) {
+        const int t = w / 3, ax = w - t * 3;
+        double s = 0.0;
+        for (int k = 0; k < nch; ++k) s += part[(t * 3 + ax) * nch + k];
+        atomicAdd(d.grad + 3 * tatom + ax, s);
+        atomicAdd(d.grad + 3 * __ldg(d.aux_atom + aux0 + t) + ax, -s);
+      }
+      continue;
+    }
     if (d.digest) {
       // ---- DF-J digestion (Sec. 3): the block never leaves shared memory.
       const int4 pao = __ldg(d.pair_ao + pair);
       const double wg = pao.z ? 1.0 : 2.0, wj = pao.z ? 0.5 : 1.0;
       const int nA = d.onA, nB = d.onB, nC = d.nC;
       // gamma_P: items (t, C), each a dot product over the (A, B) block with D
-      {
+      if (d.gamma) {
         FDiv fC;
         fC.init(nC);
         const unsigned n = (unsigned)(tv * nC);
@@ -548,7 +605,7 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
         }
       }
       // J_ab: items (A, B, group of 32 ket shells)
-      {
+      if (d.J) {
         const int ng = (tv + 31) / 32;
         FDiv fG2, fB2;
         fG2.init(ng);
@@ -617,10 +674,10 @@ cudaError_t init_constants() {
 }
 
 cudaError_t launch_pair_precompute(const DevBasis& orb, const int32_t* pairs, long long npair, int Ka, int Kb,
-                                   double* rec, double* ab, cudaStream_t st) {
+                                   double* rec, double* ab, cudaStream_t st, int scale_a, int scale_b) {
   long long n = npair * Ka * Kb;
   if (n == 0) return cudaSuccess;
-  pair_precompute<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(orb, pairs, npair, Ka, Kb, rec, ab);
+  pair_precompute<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(orb, pairs, npair, Ka, Kb, rec, ab, scale_a, scale_b);
   return cudaGetLastError();
 }
 

@@ -108,6 +108,20 @@ struct ClassDesc {
   double* J;
   const int4* pair_ao;     // per pair: {ao_a, ao_b, a == b, 0}
   const int* aux_ao;       // per ket-list entry: first AO
+  // Gradient digestion (digest == 2): the block is a Cartesian-bra derivative
+  // class ((la+-1, lb) or (la, lb+-1) in the caller's order); each entry of
+  // gmap = {a', b', index into the Cartesian weight block Dc[a][b], factor}
+  // adds factor * Dc[a][b] * sum_C c_C I[a'][b'][C] to dE/d(centre)_axis;
+  // entries are grouped by axis (gstart[0..3]).
+  int g_centre;            // 0: derivative on the pair's first shell, 1: second
+  int g_nAp, g_ncA, g_nBp, g_ncB, g_nch, g_base;
+  int gstart[4];
+  const int4* gmap;
+  const double* Ta;        // [2la+1][ncart(la)] of the original la
+  const double* Tb;
+  double* grad;            // [natom][3]
+  const int2* pair_atoms;  // per pair: atoms of the two shells
+  const int* aux_atom;     // per ket-list entry
 };
 
 // Device view of a basis (shell tables in HBM).

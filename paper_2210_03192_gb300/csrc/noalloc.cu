@@ -20,7 +20,7 @@
 namespace lx3c {
 cudaError_t init_constants();
 cudaError_t launch_pair_precompute(const DevBasis& orb, const int32_t* pairs, long long npair, int Ka, int Kb,
-                                   double* rec, double* ab, cudaStream_t st);
+                                   double* rec, double* ab, cudaStream_t st, int scale_a = 0, int scale_b = 0);
 cudaError_t launch_aux_precompute(const DevBasis& aux, const int32_t* auxs, long long naux, int Kc, double* rec,
                                   double* cxyz, cudaStream_t st);
 cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st);
