@@ -58,6 +58,7 @@ typedef int lx3c_status;
 typedef struct lx3c_basis lx3c_basis;
 typedef struct lx3c_plan lx3c_plan;
 typedef struct lx3c_dfj lx3c_dfj;
+typedef struct lx3c_batch lx3c_batch;
 
 /* Thread-local description of the last failure in this thread. */
 const char* lx3c_last_error(void);
@@ -180,9 +181,11 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  *   atomic arrival order.
  * lx3c_dfj_energy: gamma as above (J skipped) and *energy = c^T gamma
  *   (device scalar), the DF-J energy whose gradient lx3c_dfj_grad returns.
- * lx3c_dfj_info: out[0..9] = groups, screened (pair, ket shell) triples,
+ * lx3c_dfj_info: out[0..10] = groups, screened (pair, ket shell) triples,
  *   integrals digested, algorithmic FP64 flops per execute, kernel launches
- *   per execute, nao, naux_ao, natom, gradient FP64 flops, gradient launches.
+ *   per execute, nao, naux_ao, natom, gradient FP64 flops, gradient launches,
+ *   tile slots of the integral launches (screened triples / slots is the
+ *   tile fill).
  * lx3c_dfj_grad: dE/dR for E = c^T gamma with D and c held fixed (not in the
  *   paper): for every screened triple the derivative integrals
  *   d/dA (ab|P) = sum_prim [2 za (a+1 b|P) - a (a-1 b|P)] (same for B) are
@@ -206,6 +209,47 @@ lx3c_status lx3c_dfj_info(const lx3c_dfj* plan, double* out, int n);
 lx3c_status lx3c_dfj_group(const lx3c_dfj* plan, int gi, int32_t* info, int32_t* pairs, int32_t* counts,
                            int32_t* auxs);
 void lx3c_dfj_destroy(lx3c_dfj* plan);
+
+/*
+ * Batched uneven workload (not in the paper; the paper launches one class per
+ * kernel): DF-J builds of several molecules, every class mixed, run from one
+ * CUDA graph launch.
+ *
+ * lx3c_batch_plan: one DF-J plan per molecule (orbs[m], auxs[m], screening as
+ *   in lx3c_dfj_plan), then an autotuner picks the triples-per-tile shape of
+ *   every launch signature (class, orientation, contraction, Kc) by timing
+ *   candidates on a fixed prefix (about eight waves of tiles) of the
+ *   signature's largest launch; results are read from and written to the
+ *   text file tune_cache ("key T" lines) when it is non-NULL.  Setup;
+ *   synchronises `stream`.
+ * lx3c_batch_bind: fixes the per-molecule device buffers (D[m] nao x nao,
+ *   c[m] naux_ao in; gamma[m], J[m] out; all owned by the caller and kept
+ *   alive while the batch is executed), orders the class launches longest
+ *   first and captures two CUDA graphs of the whole build (zeroing,
+ *   precompute, integrals, J symmetrisation): graph 1 runs every
+ *   (class launch, tile) work item in ONE persistent kernel that pulls items
+ *   from an atomic counter (no CTA waits on another); graph 2 runs the class
+ *   launches themselves on four parallel graph branches.  Setup; may
+ *   synchronise.  Returns LX3C_ECUDA if a capture fails.
+ * lx3c_batch_execute: mode 1 or 2 launches graph 1 or 2 (one
+ *   cudaGraphLaunch on `stream`); mode 0 runs the same tasks as per-class
+ *   launches (lx3c_dfj_execute per molecule), for comparison; any other mode
+ *   is LX3C_EINVAL.  Asynchronous.
+ * lx3c_batch_info: out[0..13] = molecules, screened triples, integrals,
+ *   algorithmic flops, plain kernel launches, persistent-graph kernel nodes,
+ *   work items, class launches merged, persistent smem bytes, persistent
+ *   grid, tuned signatures, signatures measured by this plan, branch-graph
+ *   kernel nodes, branches, tile slots (tiles x triples per tile, summed
+ *   over launches; screened triples / slots is the tile fill).
+ */
+lx3c_status lx3c_batch_plan(lx3c_batch** out, int nmol, const lx3c_basis* const* orbs,
+                            const lx3c_basis* const* auxs, double schwarz_tol, const char* tune_cache,
+                            void* stream);
+lx3c_status lx3c_batch_bind(lx3c_batch* batch, const double* const* D, const double* const* c,
+                            double* const* gamma, double* const* J, void* stream);
+lx3c_status lx3c_batch_execute(lx3c_batch* batch, int mode, void* stream);
+lx3c_status lx3c_batch_info(const lx3c_batch* batch, double* out, int n);
+void lx3c_batch_destroy(lx3c_batch* batch);
 
 /*
  * Allocation-free form of one (la lb|lc) class evaluation.  The paper has no

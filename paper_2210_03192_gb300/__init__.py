@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import LibraryError, check, ptr
 from . import workloads  # noqa: F401  (seeded input generators)
 
-__all__ = ["DeviceBasis", "Eri3cPlan", "DFJPlan", "DFJEnergy", "eri3c", "eri3c_host", "boys", "class_flops", "solid_harmonics",
+__all__ = ["DeviceBasis", "Eri3cPlan", "DFJPlan", "DFJEnergy", "Batch", "eri3c", "eri3c_host", "boys", "class_flops", "solid_harmonics",
            "cvrr2_expansion", "LibraryError", "workloads"]
 
 
@@ -154,11 +154,12 @@ class DFJPlan:
         self.handle = ctypes.c_void_p()
         check(L.lx3c_dfj_plan(ctypes.byref(self.handle), self.orb.handle, self.aux.handle, float(schwarz_tol),
                               1 if gradient else 0, _stream_handle(stream)), "lx3c_dfj_plan")
-        info = np.zeros(10)
-        check(L.lx3c_dfj_info(self.handle, ptr(info), 10), "lx3c_dfj_info")
+        info = np.zeros(11)
+        check(L.lx3c_dfj_info(self.handle, ptr(info), 11), "lx3c_dfj_info")
         self.ngroups, self.ntasks, self.nint, self.flops, self.launches, self.nao, self.naux_ao = (
             int(info[0]), int(info[1]), float(info[2]), float(info[3]), int(info[4]), int(info[5]), int(info[6]))
         self.natom, self.grad_flops, self.grad_launches = int(info[7]), float(info[8]), int(info[9])
+        self.tile_fill = float(info[1]) / max(float(info[10]), 1.0)
 
     def energy(self, D, c, stream=None):
         """E = c^T gamma (device scalar tensor) and gamma."""
@@ -222,6 +223,54 @@ class DFJPlan:
         h = getattr(self, "handle", None)
         if h is not None and h.value and _lib._lib is not None:
             _lib._lib.lx3c_dfj_destroy(h)
+            self.handle = None
+
+
+class Batch:
+    """Several molecules' DF-J builds as one persistent, graph-captured launch.
+
+    Batch([(orb, aux), ...], schwarz_tol, tune_cache).bind(Ds, cs) then
+    .execute(mode) with mode 1 (one graph, one persistent kernel), 2 (one
+    graph, class launches on parallel branches) or 0 (per-class launches)."""
+
+    INFO = ["molecules", "tasks", "integrals", "flops", "plain_launches", "graph_kernels", "work_items",
+            "class_launches", "smem", "grid", "tuned", "measured", "branch_kernels", "branches", "slots"]
+
+    def __init__(self, mols, schwarz_tol=1e-12, tune_cache=None, stream=None):
+        L = _lib.load()
+        self._bases = [(o if isinstance(o, DeviceBasis) else DeviceBasis(o, stream),
+                        a if isinstance(a, DeviceBasis) else DeviceBasis(a, stream)) for o, a in mols]
+        orbs = (ctypes.c_void_p * len(mols))(*[o.handle.value for o, _ in self._bases])
+        auxs = (ctypes.c_void_p * len(mols))(*[a.handle.value for _, a in self._bases])
+        self.handle = ctypes.c_void_p()
+        check(L.lx3c_batch_plan(ctypes.byref(self.handle), len(mols), ctypes.cast(orbs, ctypes.c_void_p),
+                                ctypes.cast(auxs, ctypes.c_void_p), float(schwarz_tol),
+                                tune_cache.encode() if tune_cache else None, _stream_handle(stream)), "lx3c_batch_plan")
+        self.nmol = len(mols)
+
+    def info(self):
+        out = np.zeros(len(self.INFO))
+        check(_lib.load().lx3c_batch_info(self.handle, ptr(out), len(self.INFO)), "lx3c_batch_info")
+        return dict(zip(self.INFO, [float(x) for x in out]))
+
+    def bind(self, Ds, cs, stream=None):
+        torch = _torch()
+        self.D, self.c = list(Ds), list(cs)
+        self.gamma = [torch.empty(c.numel(), dtype=torch.float64, device=c.device) for c in cs]
+        self.J = [torch.empty_like(D) for D in Ds]
+        arr = lambda ts: ctypes.cast((ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts]), ctypes.c_void_p)
+        check(_lib.load().lx3c_batch_bind(self.handle, arr(self.D), arr(self.c), arr(self.gamma), arr(self.J),
+                                          _stream_handle(stream)), "lx3c_batch_bind")
+        return self
+
+    def execute(self, mode=1, stream=None):
+        check(_lib.load().lx3c_batch_execute(self.handle, int(mode), _stream_handle(stream)), "lx3c_batch_execute")
+        return self.gamma, self.J
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.lx3c_batch_destroy(h)
             self.handle = None
 
 

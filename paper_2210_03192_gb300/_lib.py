@@ -50,6 +50,12 @@ EXPORTS = {
     "lx3c_dfj_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lx3c_dfj_group": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
     "lx3c_dfj_destroy": (None, [ctypes.c_void_p]),
+    "lx3c_batch_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_double, ctypes.c_char_p, ctypes.c_void_p]),
+    "lx3c_batch_bind": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "lx3c_batch_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "lx3c_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "lx3c_batch_destroy": (None, [ctypes.c_void_p]),
     "lx3c_cvrr2_expansion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int32)]),
 }

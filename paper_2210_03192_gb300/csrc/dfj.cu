@@ -16,7 +16,10 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <map>
 #include <memory>
 #include <string>
@@ -33,6 +36,9 @@ cudaError_t launch_aux_precompute(const DevBasis& aux, const int32_t* auxs, long
                                   double* cxyz, cudaStream_t st);
 cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st);
 int eri3c_occupancy(int smem_bytes);
+cudaError_t launch_persistent(const ClassDesc* descs, const int2* work, long long nwork, unsigned long long* counter,
+                              int grid, int smem_bytes, cudaStream_t st);
+int persistent_occupancy(int smem_bytes);
 }  // namespace lx3c
 
 using namespace lx3c;
@@ -123,6 +129,8 @@ struct DfjLaunch {
   int4* d_sub = nullptr;
   int* d_prim = nullptr;
   int4* d_tiles = nullptr;
+  std::vector<int4> sub;   // host copy of the sub-pair list (re-tiling)
+  int kmax = 0;
 };
 
 struct DfjGroup {
@@ -365,6 +373,8 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
         for (int a0 = 0; a0 < cnt; a0 += d.T) tiles.push_back(int4{(int)s, a0, std::min(d.T, cnt - a0), 0});
       }
       L.ntiles = (long long)tiles.size();
+      L.sub = sub[o];
+      L.kmax = kmax[o];
       DCUDA(cudaMalloc(&L.d_sub, sub[o].size() * sizeof(int4)));
       DCUDA(cudaMalloc(&L.d_prim, std::max<size_t>(prim[o].size(), 1) * sizeof(int)));
       DCUDA(cudaMalloc(&L.d_tiles, tiles.size() * sizeof(int4)));
@@ -563,8 +573,9 @@ lx3c_status lx3c_dfj_grad(lx3c_dfj* p, const double* D, const double* c, double*
 
 lx3c_status lx3c_dfj_info(const lx3c_dfj* p, double* out, int n) {
   if (!p || (!out && n > 0)) return dfail(LX3C_EINVAL, "null pointer");
-  double tasks = 0, nint = 0, flops = 0, launches = 1, gflops = 0, glaunches = 0;
+  double tasks = 0, nint = 0, flops = 0, launches = 1, gflops = 0, glaunches = 0, slots = 0;
   for (auto& g : p->groups) {
+    for (auto& L : g.L) slots += (double)L.ntiles * L.desc.T;
     tasks += (double)g.ntasks;
     nint += g.nint;
     flops += g.flops;
@@ -574,8 +585,8 @@ lx3c_status lx3c_dfj_info(const lx3c_dfj* p, double* out, int n) {
     for (auto& dv : g.deriv) glaunches += 1 + (dv.L[0].ntiles > 0) + (dv.L[1].ntiles > 0);
   }
   const double v[] = {(double)p->groups.size(), tasks, nint, flops, launches, (double)p->nao, (double)p->naux_ao,
-                      (double)p->natom, gflops, glaunches};
-  for (int i = 0; i < n && i < 10; ++i) out[i] = v[i];
+                      (double)p->natom, gflops, glaunches, slots};
+  for (int i = 0; i < n && i < 11; ++i) out[i] = v[i];
   return LX3C_OK;
 }
 
@@ -591,6 +602,407 @@ lx3c_status lx3c_dfj_group(const lx3c_dfj* p, int gi, int32_t* info, int32_t* pa
   if (pairs) std::memcpy(pairs, g.pairs.data(), g.pairs.size() * 4);
   if (counts) std::memcpy(counts, g.counts.data(), g.counts.size() * 4);
   if (auxs) std::memcpy(auxs, g.auxs.data(), g.auxs.size() * 4);
+  return LX3C_OK;
+}
+
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched uneven workloads: several molecules' DF-J builds, every class mixed,
+// as one persistent kernel captured in a CUDA graph (not in the paper).
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Shape of one (class, orientation, kmax, Kc) launch: triples per tile T.
+std::string shape_key(const ClassDesc& d) {
+  char b[96];
+  std::snprintf(b, sizeof(b), "%d,%d,%d,%d,%d,%d,%d", d.la, d.lb, d.lc, d.bra_pure, d.Kab, d.Kc, d.digest);
+  return b;
+}
+
+// Re-tile one launch for triples-per-tile T (other shape fields recomputed by
+// the planner for that T); returns false if T does not fit.
+bool retile(DfjLaunch& L, const DfjGroup& g, const DevState* ds, int T) {
+  const ClassTables& ct = class_tables(L.desc.la, L.desc.lb, L.desc.lc, L.desc.bra_pure);
+  ClassDesc d = L.desc;
+  const int mode = T >= 32 ? 0 : 1;
+  // keep G from the planner's choice for this T
+  LaunchShape sh = choose_shape(ct, L.kmax, d.Kc, T, dev_smem(ds));
+  sh.T = T;
+  sh.mode = mode;
+  ClassDesc nd = d;
+  fill_layout(nd, ct, sh);
+  int extra = d.digest == 2 ? (d.g_nAp * d.g_ncB + d.g_ncA * d.g_ncB) : 0;
+  if (d.digest == 2) {
+    nd.g_base = nd.smem_doubles;
+    nd.smem_doubles += extra + T * 3 * d.g_nch;
+  }
+  if ((long long)nd.smem_doubles * 8 > 232448 - 64) return false;
+  nd.nchunk = (nd.K + nd.G - 1) / nd.G;
+  std::vector<int4> tiles;
+  for (size_t s2 = 0; s2 < L.sub.size(); ++s2) {
+    const int cnt = g.counts[L.sub[s2].x];
+    for (int a0 = 0; a0 < cnt; a0 += T) tiles.push_back(int4{(int)s2, a0, std::min(T, cnt - a0), 0});
+  }
+  int4* dt = nullptr;
+  if (cudaMalloc(&dt, tiles.size() * sizeof(int4)) != cudaSuccess) return false;
+  cudaMemcpy(dt, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  cudaFree(L.d_tiles);
+  L.d_tiles = dt;
+  L.ntiles = (long long)tiles.size();
+  nd.tiles = dt;
+  nd.ntiles = L.ntiles;
+  L.desc = nd;
+  const int occ = eri3c_occupancy(nd.smem_doubles * 8);
+  L.grid = (int)std::min<long long>(L.ntiles, (long long)dev_nsm(ds) * occ * 8);
+  return true;
+}
+
+}  // namespace
+
+struct lx3c_batch {
+  std::vector<lx3c_dfj*> mols;
+  DevState* ds = nullptr;
+  std::map<std::string, int> tuned;   // shape_key -> T
+  int ntuned_measured = 0;
+  // bound state
+  ClassDesc* d_descs = nullptr;
+  int2* d_work = nullptr;
+  unsigned long long* d_counter = nullptr;
+  long long nwork = 0;
+  int ndesc = 0;
+  int smem = 0;
+  int grid = 0;
+  cudaGraph_t graph = nullptr;        // mode 1: one persistent kernel
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph2 = nullptr;       // mode 2: class launches on parallel branches
+  cudaGraphExec_t exec2 = nullptr;
+  long long branch_kernels = 0;
+  std::vector<const double*> D, c;
+  std::vector<double*> gamma, J;
+  long long plain_launches = 0, graph_kernels = 0;
+};
+
+namespace {
+
+constexpr int kBranches = 4;
+
+// Mode 2: the same build as a graph whose class launches (the one-class kernel,
+// descriptor in the parameter space) are spread over kBranches parallel
+// branches, longest first onto the least loaded branch; zeroing and
+// precomputes come before the fork, J symmetrisation after the join.
+cudaError_t capture_branches(lx3c_batch* b, const std::vector<ClassDesc>& descs, const std::vector<int>& grids,
+                             const std::vector<std::pair<double, int>>& order, cudaStream_t cap) {
+  if (b->exec2) { cudaGraphExecDestroy(b->exec2); b->exec2 = nullptr; }
+  if (b->graph2) { cudaGraphDestroy(b->graph2); b->graph2 = nullptr; }
+  cudaStream_t br[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
+  cudaError_t ce = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int i = 0; i < kBranches && ce == cudaSuccess; ++i) {
+    ce = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+  }
+  if (ce == cudaSuccess) ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (ce == cudaSuccess) {
+    long long kernels = 0;
+    const int nmol = (int)b->mols.size();
+    for (int m = 0; m < nmol; ++m) {
+      lx3c_dfj* p = b->mols[m];
+      cudaMemsetAsync(b->gamma[m], 0, p->naux_ao * 8, cap);
+      cudaMemsetAsync(b->J[m], 0, p->nao * p->nao * 8, cap);
+      for (auto& g : p->groups) {
+        launch_pair_precompute(p->orb->dev(), g.d_pairs, (long long)g.counts.size(), g.Ka, g.Kb, g.d_pairrec,
+                               g.d_pairab, cap);
+        launch_aux_precompute(p->aux->dev(), g.d_auxs, (long long)g.auxs.size(), g.Kc, g.d_auxrec, g.d_auxc, cap);
+        kernels += 2;
+      }
+    }
+    cudaEventRecord(fork, cap);
+    double load[kBranches] = {};
+    for (int i = 0; i < kBranches; ++i) cudaStreamWaitEvent(br[i], fork, 0);
+    for (auto& o : order) {
+      int k = 0;
+      for (int i = 1; i < kBranches; ++i)
+        if (load[i] < load[k]) k = i;
+      load[k] += o.first;
+      launch_eri3c(descs[o.second], grids[o.second], br[k]);
+      ++kernels;
+    }
+    for (int i = 0; i < kBranches; ++i) {
+      cudaEventRecord(join[i], br[i]);
+      cudaStreamWaitEvent(cap, join[i], 0);
+    }
+    for (int m = 0; m < nmol; ++m) {
+      dim3 blk(32, 8), grd((unsigned)((b->mols[m]->nao + 31) / 32), (unsigned)((b->mols[m]->nao + 7) / 8));
+      symmetrize<<<grd, blk, 0, cap>>>(b->J[m], b->mols[m]->nao);
+      ++kernels;
+    }
+    ce = cudaStreamEndCapture(cap, &b->graph2);
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec2, b->graph2, 0);
+    b->branch_kernels = kernels;
+  }
+  for (int i = 0; i < kBranches; ++i) {
+    if (br[i]) cudaStreamDestroy(br[i]);
+    if (join[i]) cudaEventDestroy(join[i]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  return ce;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lx3c_batch_destroy(lx3c_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->exec2) cudaGraphExecDestroy(b->exec2);
+  if (b->graph2) cudaGraphDestroy(b->graph2);
+  cudaFree(b->d_descs);
+  cudaFree(b->d_work);
+  cudaFree(b->d_counter);
+  for (auto* m : b->mols) lx3c_dfj_destroy(m);
+  delete b;
+}
+
+lx3c_status lx3c_batch_plan(lx3c_batch** out, int nmol, const lx3c_basis* const* orbs, const lx3c_basis* const* auxs,
+                            double schwarz_tol, const char* tune_cache, void* stream) {
+  if (!out) return dfail(LX3C_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (nmol <= 0 || !orbs || !auxs) return dfail(LX3C_EINVAL, "empty molecule list");
+  std::unique_ptr<lx3c_batch> b(new lx3c_batch);
+  int rc = device_state_get(&b->ds);
+  if (rc) return rc;
+  for (int m = 0; m < nmol; ++m) {
+    lx3c_dfj* p = nullptr;
+    rc = lx3c_dfj_plan(&p, orbs[m], auxs[m], schwarz_tol, 0, stream);
+    if (rc) return rc;
+    b->mols.push_back(p);
+  }
+  // ---- autotuner: triples per tile for each launch signature, timed on the
+  // signature's largest launch; results cached as "key T" lines.
+  std::map<std::string, int> cache;
+  if (tune_cache && *tune_cache) {
+    std::ifstream f(tune_cache);
+    std::string k;
+    int T;
+    while (f >> k >> T) cache[k] = T;
+  }
+  std::map<std::string, std::pair<DfjLaunch*, DfjGroup*>> biggest;
+  for (auto* p : b->mols)
+    for (auto& g : p->groups)
+      for (auto& L : g.L) {
+        if (!L.ntiles) continue;
+        const std::string k = shape_key(L.desc);
+        auto it = biggest.find(k);
+        long long work = (long long)L.desc.T * L.ntiles;
+        if (it == biggest.end() || (long long)it->second.first->desc.T * it->second.first->ntiles < work)
+          biggest[k] = {&L, &g};
+      }
+  cudaStream_t st = (cudaStream_t)stream;
+  double *tg = nullptr, *tJ = nullptr, *tD = nullptr, *tc = nullptr;
+  bool measured = false;
+  for (auto& kv : biggest) {
+    if (cache.count(kv.first)) {
+      b->tuned[kv.first] = cache[kv.first];
+      continue;
+    }
+    DfjLaunch& L = *kv.second.first;
+    DfjGroup& g = *kv.second.second;
+    lx3c_dfj* owner = nullptr;
+    for (auto* p : b->mols)
+      for (auto& gg : p->groups)
+        if (&gg == &g) owner = p;
+    if (!tg) {
+      long long mx = 0, mxa = 0;
+      for (auto* p : b->mols) { mx = std::max(mx, p->nao); mxa = std::max(mxa, p->naux_ao); }
+      DCUDA(cudaMalloc(&tg, mxa * 8)); DCUDA(cudaMalloc(&tc, mxa * 8));
+      DCUDA(cudaMalloc(&tJ, mx * mx * 8)); DCUDA(cudaMalloc(&tD, mx * mx * 8));
+      DCUDA(cudaMemset(tc, 0, mxa * 8)); DCUDA(cudaMemset(tD, 0, mx * mx * 8));
+    }
+    DCUDA(launch_pair_precompute(owner->orb->dev(), g.d_pairs, (long long)g.counts.size(), g.Ka, g.Kb, g.d_pairrec,
+                                 g.d_pairab, st));
+    DCUDA(launch_aux_precompute(owner->aux->dev(), g.d_auxs, (long long)g.auxs.size(), g.Kc, g.d_auxrec, g.d_auxc, st));
+    const int T0 = L.desc.T;
+    std::vector<int> cands = {T0};
+    if (T0 >= 2) cands.push_back(T0 / 2);
+    if (T0 <= 256) cands.push_back(T0 * 2);
+    float best = 1e30f;
+    int bestT = T0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // time every candidate on the same prefix of sub-pairs: about 8 waves of
+    // the planner's tiles, the same triples whatever T is
+    long long nsub_t = (long long)L.sub.size();
+    {
+      const long long cap = 8LL * dev_nsm(b->ds) * 2;
+      long long nt = 0;
+      for (long long s2 = 0; s2 < (long long)L.sub.size(); ++s2) {
+        nt += (g.counts[L.sub[s2].x] + T0 - 1) / T0;
+        if (nt >= cap) { nsub_t = s2 + 1; break; }
+      }
+    }
+    for (int T : cands) {
+      if (!retile(L, g, b->ds, T)) continue;
+      ClassDesc d = L.desc;
+      d.D = tD; d.cvec = tc; d.gamma = tg; d.J = tJ;
+      long long nt = 0;
+      for (long long s2 = 0; s2 < nsub_t; ++s2) nt += (g.counts[L.sub[s2].x] + T - 1) / T;
+      d.ntiles = nt;
+      const int grid = (int)std::min<long long>(nt, L.grid);
+      launch_eri3c(d, grid, st);
+      cudaEventRecord(e0, st);
+      launch_eri3c(d, grid, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bestT = T; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tuned[kv.first] = bestT;
+    cache[kv.first] = bestT;
+    measured = true;
+    ++b->ntuned_measured;
+  }
+  cudaFree(tg); cudaFree(tJ); cudaFree(tD); cudaFree(tc);
+  // apply the tuned shapes to every launch
+  for (auto* p : b->mols)
+    for (auto& g : p->groups)
+      for (auto& L : g.L) {
+        if (!L.ntiles) continue;
+        auto it = b->tuned.find(shape_key(L.desc));
+        if (it != b->tuned.end() && it->second != L.desc.T) retile(L, g, b->ds, it->second);
+      }
+  if (measured && tune_cache && *tune_cache) {
+    std::ofstream f(tune_cache);
+    for (auto& kv : cache) f << kv.first << " " << kv.second << "\n";
+  }
+  DCUDA(cudaGetLastError());
+  DCUDA(cudaStreamSynchronize(st));
+  *out = b.release();
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_batch_bind(lx3c_batch* b, const double* const* D, const double* const* c, double* const* gamma,
+                            double* const* J, void* stream) {
+  if (!b || !D || !c || !gamma || !J) return dfail(LX3C_EINVAL, "null pointer");
+  const int nmol = (int)b->mols.size();
+  b->D.assign(D, D + nmol); b->c.assign(c, c + nmol);
+  b->gamma.assign(gamma, gamma + nmol); b->J.assign(J, J + nmol);
+  // descriptors with this binding's pointers, and the longest-first work list
+  std::vector<ClassDesc> descs;
+  std::vector<int> grids;
+  std::vector<std::pair<double, int>> order;
+  int smem = 0;
+  b->plain_launches = 0;
+  for (int m = 0; m < nmol; ++m) {
+    lx3c_dfj* p = b->mols[m];
+    b->plain_launches += 1;
+    for (auto& g : p->groups) {
+      b->plain_launches += 2;
+      for (auto& L : g.L) {
+        if (!L.ntiles) continue;
+        ++b->plain_launches;
+        ClassDesc d = L.desc;
+        d.D = D[m]; d.cvec = c[m]; d.gamma = gamma[m]; d.J = J[m];
+        double fl = 0;
+        lx3c_class_flops(d.la, d.lb, d.lc, d.Kab, d.Kc, 1, &fl);
+        order.push_back({fl * (double)d.T * (double)L.ntiles, (int)descs.size()});
+        descs.push_back(d);
+        grids.push_back(L.grid);
+        smem = std::max(smem, d.smem_doubles * 8);
+      }
+    }
+  }
+  std::stable_sort(order.begin(), order.end(), [](auto& x, auto& y) { return x.first > y.first; });
+  std::vector<int2> work;
+  for (auto& o : order)
+    for (long long t = 0; t < descs[o.second].ntiles; ++t) work.push_back(int2{o.second, (int)t});
+  cudaFree(b->d_descs);
+  cudaFree(b->d_work);
+  if (!b->d_counter) DCUDA(cudaMalloc(&b->d_counter, sizeof(unsigned long long)));
+  DCUDA(cudaMalloc(&b->d_descs, descs.size() * sizeof(ClassDesc)));
+  DCUDA(cudaMalloc(&b->d_work, std::max<size_t>(work.size(), 1) * sizeof(int2)));
+  DCUDA(cudaMemcpy(b->d_descs, descs.data(), descs.size() * sizeof(ClassDesc), cudaMemcpyHostToDevice));
+  DCUDA(cudaMemcpy(b->d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  b->nwork = (long long)work.size();
+  b->ndesc = (int)descs.size();
+  b->smem = smem;
+  b->grid = dev_nsm(b->ds) * persistent_occupancy(smem);
+  // capture the whole batched build in one graph
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  cudaStream_t cap;
+  DCUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  DCUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  b->graph_kernels = 0;
+  for (int m = 0; m < nmol; ++m) {
+    lx3c_dfj* p = b->mols[m];
+    cudaMemsetAsync(gamma[m], 0, p->naux_ao * 8, cap);
+    cudaMemsetAsync(J[m], 0, p->nao * p->nao * 8, cap);
+    for (auto& g : p->groups) {
+      launch_pair_precompute(p->orb->dev(), g.d_pairs, (long long)g.counts.size(), g.Ka, g.Kb, g.d_pairrec,
+                             g.d_pairab, cap);
+      launch_aux_precompute(p->aux->dev(), g.d_auxs, (long long)g.auxs.size(), g.Kc, g.d_auxrec, g.d_auxc, cap);
+      b->graph_kernels += 2;
+    }
+  }
+  cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), cap);
+  launch_persistent(b->d_descs, b->d_work, b->nwork, b->d_counter, b->grid, b->smem, cap);
+  b->graph_kernels += 1;
+  for (int m = 0; m < nmol; ++m) {
+    dim3 blk(32, 8), grd((unsigned)((b->mols[m]->nao + 31) / 32), (unsigned)((b->mols[m]->nao + 7) / 8));
+    symmetrize<<<grd, blk, 0, cap>>>(J[m], b->mols[m]->nao);
+    b->graph_kernels += 1;
+  }
+  cudaError_t ce = cudaStreamEndCapture(cap, &b->graph);
+  if (ce != cudaSuccess) {
+    cudaStreamDestroy(cap);
+    return dfail(LX3C_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  }
+  ce = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (ce == cudaSuccess) ce = capture_branches(b, descs, grids, order, cap);
+  cudaStreamDestroy(cap);
+  if (ce != cudaSuccess) return dfail(LX3C_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  (void)stream;
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_batch_execute(lx3c_batch* b, int mode, void* stream) {
+  if (!b) return dfail(LX3C_EINVAL, "null batch");
+  if (b->D.empty()) return dfail(LX3C_EINVAL, "batch not bound (lx3c_batch_bind)");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mode == 1 || mode == 2) {
+    DCUDA(cudaGraphLaunch(mode == 1 ? b->exec : b->exec2, st));
+    return LX3C_OK;
+  }
+  if (mode != 0) return dfail(LX3C_EINVAL, "mode must be 0, 1 or 2");
+  for (size_t m = 0; m < b->mols.size(); ++m) {
+    lx3c_status rc = lx3c_dfj_execute(b->mols[m], b->D[m], b->c[m], b->gamma[m], b->J[m], stream);
+    if (rc) return rc;
+  }
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_batch_info(const lx3c_batch* b, double* out, int n) {
+  if (!b || (!out && n > 0)) return dfail(LX3C_EINVAL, "null pointer");
+  double tasks = 0, nint = 0, flops = 0, slots = 0;
+  for (auto* p : b->mols)
+    for (auto& g : p->groups) {
+      tasks += (double)g.ntasks; nint += g.nint; flops += g.flops;
+      for (auto& L : g.L) slots += (double)L.ntiles * L.desc.T;
+    }
+  const double v[] = {(double)b->mols.size(), tasks, nint, flops, (double)b->plain_launches,
+                      (double)b->graph_kernels, (double)b->nwork, (double)b->ndesc, (double)b->smem,
+                      (double)b->grid, (double)b->tuned.size(), (double)b->ntuned_measured,
+                      (double)b->branch_kernels, (double)kBranches, slots};
+  for (int i = 0; i < n && i < 15; ++i) out[i] = v[i];
   return LX3C_OK;
 }
 

@@ -205,8 +205,9 @@ __device__ __forceinline__ void dec3(unsigned w, int mode, const FDiv& fT, const
   }
 }
 
-__global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__ ClassDesc d) {
-  extern __shared__ double sm[];
+// One tile: (sub-pair, up to T ket shells) through every stage, ending in the
+// store, the DF-J digestion or the gradient digestion.
+__device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, double* sm) {
   const unsigned tid = threadIdx.x;
   const int T = d.T, G = d.G, mode = d.mode, lc = d.lc, Lab = d.Lab;
   FDiv fT, fG, fKc;
@@ -214,8 +215,7 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
   fG.init(G);
   fKc.init(d.Kc);
   const int auxsz = 3 + kAuxRec * d.Kc;
-
-  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
+  {
     long long sub;
     int aux0, tv;
     if (d.tiles) {
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
         atomicAdd(d.grad + 3 * tatom + ax, s);
         atomicAdd(d.grad + 3 * __ldg(d.aux_atom + aux0 + t) + ax, -s);
       }
-      continue;
+      return;
     }
     if (d.digest) {
       // ---- DF-J digestion (Sec. 3): the block never leaves shared memory.
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
           atomicAdd(d.J + (long long)(pao.x + A) * d.ldD + pao.y + B, wj * s);
         }
       }
-      continue;
+      return;
     }
     // ---- store the tile's contiguous output block (transposed into the
     // caller's (A, B) order for B-oriented sub-pairs; added to the block
@@ -652,6 +652,45 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
         o[w] = v;
       }
     }
+  }
+}
+
+// One class launch: CTAs stride over the class's tiles.
+__global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__ ClassDesc d) {
+  extern __shared__ double sm[];
+  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body(d, tile, sm);
+}
+
+// Persistent form for mixed workloads: every CTA pulls (descriptor, tile)
+// work items from one atomic counter until the list is exhausted (items are
+// ordered longest first on the host).  No CTA ever waits on another.  The
+// item's descriptor is staged in shared memory (re-copied only when the class
+// changes), so the tile body reads its fields from there, not from global
+// memory.
+__global__ void __launch_bounds__(kThreads) eri3c_persistent(const ClassDesc* __restrict__ descs,
+                                                             const int2* __restrict__ work, long long nwork,
+                                                             unsigned long long* __restrict__ counter) {
+  extern __shared__ double sm[];
+  __shared__ __align__(16) ClassDesc sd;
+  __shared__ long long next;
+  int cur = -1;
+  constexpr int kWords = (int)(sizeof(ClassDesc) / 8);
+  static_assert(sizeof(ClassDesc) % 8 == 0, "descriptor copy in 8-byte words");
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) next = (long long)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const long long w = next;
+    if (w >= nwork) return;
+    const int2 wk = work[w];
+    if (wk.x != cur) {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(descs + wk.x);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sd);
+      for (int i = threadIdx.x; i < kWords; i += kThreads) dst[i] = src[i];
+      cur = wk.x;
+      __syncthreads();
+    }
+    tile_body(sd, wk.y, sm);
   }
 }
 
@@ -705,6 +744,23 @@ cudaError_t launch_boys(const double* T, long long n, int mmax, const double* ta
   if (n == 0) return cudaSuccess;
   boys_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(T, n, mmax, tab, mid, cL, out);
   return cudaGetLastError();
+}
+
+// The dynamic shared-memory attribute is set by persistent_occupancy(), which
+// callers run before any stream capture.
+cudaError_t launch_persistent(const ClassDesc* descs, const int2* work, long long nwork, unsigned long long* counter,
+                              int grid, int smem_bytes, cudaStream_t st) {
+  eri3c_persistent<<<grid, kThreads, smem_bytes, st>>>(descs, work, nwork, counter);
+  return cudaGetLastError();
+}
+
+int persistent_occupancy(int smem_bytes) {
+  int nb = 0;
+  cudaFuncSetAttribute(eri3c_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       232448 - (int)sizeof(ClassDesc) - 64);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eri3c_persistent, kThreads, smem_bytes) != cudaSuccess)
+    return 1;
+  return nb < 1 ? 1 : nb;
 }
 
 int eri3c_occupancy(int smem_bytes) {

@@ -1,0 +1,79 @@
+"""Batched uneven workload (configs[3] recipe, not in the paper): several
+molecules' DF-J builds, every class mixed, as one persistent kernel inside one
+CUDA graph, checked against the per-class launches and the oracle."""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_03192_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_03192_gb300 as m
+    return m
+
+
+def normwise(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def test_batch_graph_equals_plain_and_oracle(lx):
+    mols = [W.molecule(n, 500 + n, aux_fraction=0.5) for n in (2, 3, 5)]
+    rng = np.random.default_rng(4)
+    Ds, cs = [], []
+    for cl in mols:
+        n = int(oracle.ao_offsets(cl.orb)[-1])
+        naux = int(oracle.ao_offsets(cl.aux)[-1])
+        Ds.append(torch.tensor(W.density(rng, n), device="cuda"))
+        cs.append(torch.tensor(rng.standard_normal(naux), device="cuda"))
+    cache = os.path.join(tempfile.mkdtemp(), "tune.txt")
+    b = lx.Batch([(cl.orb, cl.aux) for cl in mols], 1e-12, tune_cache=cache).bind(Ds, cs)
+    info = b.info()
+    assert info["graph_kernels"] >= 1 and info["work_items"] > 0 and info["branches"] == 4
+    assert os.path.exists(cache) and info["tuned"] > 0
+    g1, J1 = b.execute(mode=1)
+    torch.cuda.synchronize()
+    g1 = [g.cpu().numpy().copy() for g in g1]
+    J1 = [J.cpu().numpy().copy() for J in J1]
+    g2, J2 = b.execute(mode=2)
+    torch.cuda.synchronize()
+    g2 = [g.cpu().numpy().copy() for g in g2]
+    J2 = [J.cpu().numpy().copy() for J in J2]
+    g0, J0 = b.execute(mode=0)
+    torch.cuda.synchronize()
+    for m, cl in enumerate(mols):
+        for g, J in ((g1[m], J1[m]), (g2[m], J2[m])):
+            assert normwise(g, g0[m].cpu().numpy()) < 1e-13
+            assert normwise(J, J0[m].cpu().numpy()) < 1e-13
+    assert info["branch_kernels"] == info["graph_kernels"] - 1 + info["class_launches"]
+    # oracle on the smallest molecule, same screened tasks
+    cl = mols[0]
+    plan = lx.DFJPlan(cl.orb, cl.aux, 1e-12)
+    go, Jo = oracle.dfj(cl.orb, cl.aux, Ds[0].cpu().numpy(), cs[0].cpu().numpy(), tasks=plan.tasks(), mode="quad")
+    assert normwise(g1[0], go) < 1e-12
+    assert normwise(J1[0], Jo) < 1e-12
+    # a second plan reads the cache instead of measuring
+    b2 = lx.Batch([(cl.orb, cl.aux) for cl in mols], 1e-12, tune_cache=cache)
+    assert b2.info()["measured"] == 0
+
+
+def test_batch_replay_is_stable(lx):
+    mols = [W.molecule(n, 600 + n, aux_fraction=0.3) for n in (4, 8)]
+    rng = np.random.default_rng(5)
+    Ds = [torch.tensor(W.density(rng, int(oracle.ao_offsets(cl.orb)[-1])), device="cuda") for cl in mols]
+    cs = [torch.tensor(rng.standard_normal(int(oracle.ao_offsets(cl.aux)[-1])), device="cuda") for cl in mols]
+    b = lx.Batch([(cl.orb, cl.aux) for cl in mols]).bind(Ds, cs)
+    ga, _ = b.execute(1)
+    ga = [g.cpu().numpy().copy() for g in ga]
+    gb, _ = b.execute(1)
+    for x, y in zip(ga, gb):
+        assert normwise(x, y.cpu().numpy()) < 1e-13
