@@ -45,6 +45,23 @@ using namespace lx3c;
 
 namespace {
 
+// Ket-count bound for the shape chooser from the tile fill: the largest T
+// (a power of two up to 512) at which this launch's tiles hold at least 80%
+// screened triples, returned as T/2 (the chooser allows T up to twice the
+// count it is given), and never above the longest ket list.
+long long fill_bound(const std::vector<int4>& sub, const std::vector<int>& counts, int cmax) {
+  long long tot = 0;
+  for (auto& s : sub) tot += counts[s.x];
+  int pick = 1;
+  for (int T = 512; T >= 1; T /= 2) {
+    long long slots = 0;
+    for (auto& s : sub) slots += (long long)((counts[s.x] + T - 1) / T) * T;
+    if (tot * 5 >= slots * 4) { pick = T; break; }
+  }
+  return std::min<long long>(cmax, std::max(1, pick / 2));
+}
+
+
 lx3c_status dfail(lx3c_status s, const std::string& m) {
   set_last_error("dfj: " + m);
   return s;
@@ -365,7 +382,7 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
       rc = device_class_get(ds, *ct, &dc);
       if (rc) return rc;
       ClassDesc& d = L.desc;
-      if (fill_class_desc(d, *ct, *dc, ds, o, kmax[o], Kab, g.Kc, cmax) < 0)
+      if (fill_class_desc(d, *ct, *dc, ds, o, kmax[o], Kab, g.Kc, fill_bound(sub[o], g.counts, cmax)) < 0)
         return dfail(LX3C_ENOTSUP, "class does not fit in shared memory");
       std::vector<int4> tiles;
       for (size_t s = 0; s < sub[o].size(); ++s) {
@@ -442,7 +459,7 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
           rc = device_class_get(ds, *ct, &dc);
           if (rc) return rc;
           ClassDesc& d = L.desc;
-          if (fill_class_desc(d, *ct, *dc, ds, o, dk[o], Kab, g.Kc, cmax) < 0)
+          if (fill_class_desc(d, *ct, *dc, ds, o, dk[o], Kab, g.Kc, fill_bound(dsub[o], g.counts, cmax)) < 0)
             return dfail(LX3C_ENOTSUP, "derivative class does not fit in shared memory");
           const int nch = std::max(1, (nmax + 31) / 32);
           const int nAp = 2 * g.la + 1, ncA = ncart(g.la), nBp = 2 * g.lb + 1, ncB = ncart(g.lb);

@@ -212,10 +212,12 @@ def config4_sizes():
     return [int(round(20 * 20 ** (i / 15))) for i in range(16)]
 
 
-def molecule(natom, seed, orb_recipe=None, aux_recipe=None, aux_fraction=1.0, spacing=1.8, jitter=0.3):
-    """A compact jittered-grid molecule of natom atoms (first natom points of the
-    smallest near-cubic grid), orbital / aux shells from the recipes; a
-    fraction of the aux shells (uniform, seeded) is kept when aux_fraction < 1."""
+def molecule(natom, seed, orb_recipe=None, aux_recipe=None, orb_fraction=1.0, aux_fraction=1.0, spacing=1.8,
+             jitter=0.3):
+    """A compact jittered-grid molecule of natom atoms (the natom grid points
+    nearest the centre of the smallest cube that holds them), orbital / aux
+    shells from the recipes.  orb_fraction / aux_fraction < 1 keep that
+    fraction of the orbital / aux shells (uniform, seeded)."""
     orb_recipe = ORB_RECIPE_SMALL if orb_recipe is None else orb_recipe
     aux_recipe = AUX_RECIPE_BATCH if aux_recipe is None else aux_recipe
     rng = np.random.default_rng(seed)
@@ -227,15 +229,20 @@ def molecule(natom, seed, orb_recipe=None, aux_recipe=None, aux_fraction=1.0, sp
     coords = g * spacing + rng.uniform(-jitter, jitter, size=g.shape)
     orb = _atom_shells(rng, coords, orb_recipe, 0.05, 1.0e4)
     aux = _atom_shells(rng, coords, aux_recipe, 0.05, 1.0e4)
+    if orb_fraction < 1.0:
+        keep = np.sort(rng.choice(orb.nshell, size=max(1, int(round(orb_fraction * orb.nshell))), replace=False))
+        orb = orb.subset(keep)
     if aux_fraction < 1.0:
         keep = np.sort(rng.choice(aux.nshell, size=max(1, int(round(aux_fraction * aux.nshell))), replace=False))
         aux = aux.subset(keep)
     return Cluster(natom, coords, orb, aux)
 
 
-def config4(aux_fraction=0.1):
+def config4(orb_fraction=0.25):
     """Batched uneven workload: 16 molecules of 20-400 atoms, orbital 3s2p2d1f1g
     (K=6/3/1/1/1), aux 8s6p5d4f3g2h1i (K=1), every class up to (gg|i) mixed.
-    The aux shells are subsampled at a fixed fraction (identical for the
-    batched and the per-class runs) to keep one build within about a minute."""
-    return [molecule(n, SEED_BASE + 3 + 100 * i, aux_fraction=aux_fraction) for i, n in enumerate(config4_sizes())]
+    A fixed fraction of each molecule's orbital shells is kept (uniform,
+    seeded; identical for the batched and the per-class runs), which scales
+    the shell pairs by about its square and leaves every pair's ket list, and
+    so the tile fill, as in the full molecule."""
+    return [molecule(n, SEED_BASE + 3 + 100 * i, orb_fraction=orb_fraction) for i, n in enumerate(config4_sizes())]
