@@ -408,6 +408,8 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
       d.primidx = L.d_prim;
       d.pairrec = g.d_pairrec; d.pairab = g.d_pairab; d.auxrec = g.d_auxrec; d.auxc = g.d_auxc;
       d.digest = 1;
+      set_digest_scratch(d);
+      if ((long long)d.smem_doubles * 8 > 232448) return dfail(LX3C_ENOTSUP, "digestion scratch does not fit");
       d.ldD = p->nao;
       d.pair_ao = g.d_pair_ao;
       d.aux_ao = g.d_aux_ao;
@@ -655,6 +657,8 @@ bool retile(DfjLaunch& L, const DfjGroup& g, const DevState* ds, int T) {
   if (d.digest == 2) {
     nd.g_base = nd.smem_doubles;
     nd.smem_doubles += extra + T * 3 * d.g_nch;
+  } else if (d.digest == 1) {
+    set_digest_scratch(nd);
   }
   if ((long long)nd.smem_doubles * 8 > 232448 - 64) return false;
   nd.nchunk = (nd.K + nd.G - 1) / nd.G;

@@ -80,11 +80,17 @@ __device__ __forceinline__ void boys_scaled(const double* __restrict__ tab, cons
     const double* c = tab + ((size_t)i * kBoysNF + hi) * 8;
     const double* ce = tab + ((size_t)i * kBoysNF + (kBoysNF - 1)) * 8;
     FL = __ldg(c + 7);
-    ex = __ldg(ce + 7);
+    ex = 0.0;
+    if (hi > lo) {  // exp(-T) only feeds the downward relation
+      ex = __ldg(ce + 7);
 #pragma unroll
-    for (int j = 6; j >= 0; --j) {
-      FL = fma(FL, dx, __ldg(c + j));
-      ex = fma(ex, dx, __ldg(ce + j));
+      for (int j = 6; j >= 0; --j) {
+        FL = fma(FL, dx, __ldg(c + j));
+        ex = fma(ex, dx, __ldg(ce + j));
+      }
+    } else {
+#pragma unroll
+      for (int j = 6; j >= 0; --j) FL = fma(FL, dx, __ldg(c + j));
     }
   } else {
     double rs = rsqrt_fp64(T);
@@ -100,12 +106,13 @@ __device__ __forceinline__ void boys_scaled(const double* __restrict__ tab, cons
     ex = 0.0;
   }
   double G = pref * FL;
-  double E = pref * ex;
-  double T2 = T + T;
   v[(hi - lo) * stride] = G;
-  for (int m = hi - 1; m >= lo; --m) {
-    G = fma(T2, G, E) * c_inv2m1[m];
-    v[(m - lo) * stride] = G;
+  if (hi > lo) {
+    const double E = pref * ex, T2 = T + T;
+    for (int m = hi - 1; m >= lo; --m) {
+      G = fma(T2, G, E) * c_inv2m1[m];
+      v[(m - lo) * stride] = G;
+    }
   }
 }
 
@@ -205,6 +212,44 @@ __device__ __forceinline__ void dec3(unsigned w, int mode, const FDiv& fT, const
   }
 }
 
+// Segmented dot products out[o] += sum_{r < len} prod(o, r) for o < nout,
+// each partial result handed to emit(o, value), which adds it to global
+// memory with an atomic.  The FP64 pipe charges a whole warp instruction
+// whatever the number of active lanes, and one lane's dependent FMAs are
+// serialised, so the mapping follows the estimated chain length: one lane per
+// output (two partial sums) when there are many outputs, else one warp per
+// (output, 128-term chunk) whose lanes each emit their own partial sum (a warp
+// shuffle reduction here costs the whole kernel registers).
+template <class Prod, class Emit>
+__device__ __forceinline__ void seg_dot(int nout, int len, const Prod& prod, const Emit& emit) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kThreads / 32, kChunk = 128;
+  if (nout <= 0 || len <= 0) return;
+  const int nch = (len + kChunk - 1) / kChunk;
+  const long long lane_steps = (long long)((nout + kThreads - 1) / kThreads) * ((len + 1) / 2);
+  const long long warp_steps = (long long)((nout * nch + kWarps - 1) / kWarps) * ((min(len, kChunk) + 31) / 32 + 1);
+  if (lane_steps <= warp_steps) {
+    for (int o = tid; o < nout; o += kThreads) {
+      double s0 = 0.0, s1 = 0.0;
+      int r = 0;
+      for (; r + 1 < len; r += 2) {
+        s0 = prod(o, r, s0);
+        s1 = prod(o, r + 1, s1);
+      }
+      if (r < len) s0 = prod(o, r, s0);
+      emit(o, s0 + s1);
+    }
+  } else {
+    for (int it = warp; it < nout * nch; it += kWarps) {
+      const int o = it / nch, r0 = (it - o * nch) * kChunk, r1 = min(len, r0 + kChunk);
+      if (r0 + lane >= r1) continue;
+      double s = 0.0;
+      for (int r = r0 + lane; r < r1; r += 32) s = prod(o, r, s);
+      emit(o, s);
+    }
+  }
+}
+
 // One tile: (sub-pair, up to T ket shells) through every stage, ending in the
 // store, the DF-J digestion or the gradient digestion.
 __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, double* sm) {
@@ -299,9 +344,11 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
         const double pref = pr[PR_K] * ccp * rs;
         const int fb = BUF_TG(d.F, 0, g, t);
         const int fs = d.F.si;
-        sm[fb] = rg * PCx;
-        sm[fb + fs] = rg * PCy;
-        sm[fb + 2 * fs] = rg * PCz;
+        if (Lab > 0) {  // VRR1 factors (rho/gamma) PC
+          sm[fb] = rg * PCx;
+          sm[fb + fs] = rg * PCy;
+          sm[fb + 2 * fs] = rg * PCz;
+        }
         sm[fb + 3 * fs] = rg;
         if (lc > 0) {
           double X[3] = {gr * PCx, gr * PCy, gr * PCz};
@@ -390,14 +437,23 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
           const int pa0 = BUF_T(d.P, a0, t0), pa1 = BUF_T(d.P, a1, t1);
           const int vb0 = BUF_TG(d.V, (int)(e0 & 0xFFFF), 0, t0), wb0 = BUF_TG(d.W, (int)(e0 >> 16), 0, t0);
           const int vb1 = BUF_TG(d.V, (int)(e1 & 0xFFFF), 0, t1), wb1 = BUF_TG(d.W, (int)(e1 >> 16), 0, t1);
-          double acc0 = sm[pa0], acc1 = sm[pa1];
+          // FP64 instructions cost a whole warp slot, so only stored chains run
+          if (ok0 && ok1) {
+            double acc0 = sm[pa0], acc1 = sm[pa1];
 #pragma unroll 4
-          for (int g = 0; g < gcnt; ++g) {
-            acc0 = fma(sm[vb0 + g * d.V.sg], sm[wb0 + g * d.W.sg], acc0);
-            acc1 = fma(sm[vb1 + g * d.V.sg], sm[wb1 + g * d.W.sg], acc1);
+            for (int g = 0; g < gcnt; ++g) {
+              acc0 = fma(sm[vb0 + g * d.V.sg], sm[wb0 + g * d.W.sg], acc0);
+              acc1 = fma(sm[vb1 + g * d.V.sg], sm[wb1 + g * d.W.sg], acc1);
+            }
+            sm[pa0] = acc0;
+            sm[pa1] = acc1;
+          } else if (ok0 || ok1) {
+            const int pa = ok0 ? pa0 : pa1, vb = ok0 ? vb0 : vb1, wb = ok0 ? wb0 : wb1;
+            double acc = sm[pa];
+#pragma unroll 4
+            for (int g = 0; g < gcnt; ++g) acc = fma(sm[vb + g * d.V.sg], sm[wb + g * d.W.sg], acc);
+            sm[pa] = acc;
           }
-          if (ok0) sm[pa0] = acc0;
-          if (ok1) sm[pa1] = acc1;
         }
       }
       __syncthreads();
@@ -583,49 +639,49 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
     }
     if (d.digest) {
       // ---- DF-J digestion (Sec. 3): the block never leaves shared memory.
+      // With s the block's (A, B) index in its storage order:
+      //   gamma[t][C] = wg * sum_s I[t][s][C] Ds[s]        (Ds = D block)
+      //   J[s]        = wj * sum_{t,C} I[t][s][C] Cs[t][C]  (Cs = c of the tile's kets)
       const int4 pao = __ldg(d.pair_ao + pair);
       const double wg = pao.z ? 1.0 : 2.0, wj = pao.z ? 0.5 : 1.0;
-      const int nA = d.onA, nB = d.onB, nC = d.nC;
-      // gamma_P: items (t, C), each a dot product over the (A, B) block with D
-      if (d.gamma) {
-        FDiv fC;
-        fC.init(nC);
-        const unsigned n = (unsigned)(tv * nC);
-        for (unsigned w = tid; w < n; w += kThreads) {
-          const int t = (int)fC.div(w), C = (int)(w - t * nC);
-          double s = 0.0;
-          for (int A = 0; A < nA; ++A) {
-            const double* Drow = d.D + (long long)(pao.x + A) * d.ldD + pao.y;
-            for (int B = 0; B < nB; ++B) {
-              const int sidx = d.orient ? (B * nA + A) * nC + C : (A * nB + B) * nC + C;
-              s = fma(sm[BUF_T(cur, sidx, t)], __ldg(Drow + B), s);
-            }
-          }
-          atomicAdd(d.gamma + __ldg(d.aux_ao + aux0 + t) + C, wg * s);
+      const int nA = d.onA, nB = d.onB, nC = d.nC, nAB = nA * nB;
+      double* Ds = sm + d.dscr;
+      double* Cs = Ds + nAB;
+      const int sA = d.orient ? 1 : nB, sB = d.orient ? nA : 1;  // storage index of (A, B)
+      if (d.gamma)
+        for (int s = tid; s < nAB; s += kThreads) {
+          const int A = s / nB, B = s - A * nB;
+          Ds[A * sA + B * sB] = __ldg(d.D + (long long)(pao.x + A) * d.ldD + pao.y + B);
         }
-      }
-      // J_ab: items (A, B, group of 32 ket shells)
-      if (d.J) {
-        const int ng = (tv + 31) / 32;
-        FDiv fG2, fB2;
-        fG2.init(ng);
-        fB2.init(nB);
-        const unsigned n = (unsigned)(nA * nB * ng);
-        for (unsigned w = tid; w < n; w += kThreads) {
-          const int ab = (int)fG2.div(w), grp = (int)(w - ab * ng);
-          const int A = (int)fB2.div(ab), B = ab - A * nB;
-          double s = 0.0;
-          const int t1 = min(tv, grp * 32 + 32);
-          for (int t = grp * 32; t < t1; ++t) {
-            const double* cv = d.cvec + __ldg(d.aux_ao + aux0 + t);
-            for (int C = 0; C < nC; ++C) {
-              const int sidx = d.orient ? (B * nA + A) * nC + C : (A * nB + B) * nC + C;
-              s = fma(sm[BUF_T(cur, sidx, t)], __ldg(cv + C), s);
-            }
-          }
-          atomicAdd(d.J + (long long)(pao.x + A) * d.ldD + pao.y + B, wj * s);
+      if (d.J)
+        for (int i = tid; i < tv * nC; i += kThreads) {
+          const int t = i / nC, C = i - t * nC;
+          Cs[i] = __ldg(d.cvec + __ldg(d.aux_ao + aux0 + t) + C);
         }
-      }
+      __syncthreads();
+      const Buf cb = cur;
+      FDiv fC;
+      fC.init(nC);
+      if (d.gamma)
+        seg_dot(tv * nC, nAB,
+                [&](int o, int r, double acc) {
+                  const int t = (int)fC.div(o), C = o - t * nC;
+                  return fma(sm[BUF_T(cb, r * nC + C, t)], Ds[r], acc);
+                },
+                [&](int o, double v) {
+                  const int t = (int)fC.div(o), C = o - t * nC;
+                  atomicAdd(d.gamma + __ldg(d.aux_ao + aux0 + t) + C, wg * v);
+                });
+      if (d.J)
+        seg_dot(nAB, tv * nC,
+                [&](int o, int r, double acc) {
+                  const int t = (int)fC.div(r), C = r - t * nC;
+                  return fma(sm[BUF_T(cb, o * nC + C, t)], Cs[r], acc);
+                },
+                [&](int o, double v) {
+                  const int A = d.orient ? o % nA : o / nB, B = d.orient ? o / nA : o % nB;
+                  atomicAdd(d.J + (long long)(pao.x + A) * d.ldD + pao.y + B, wj * v);
+                });
       return;
     }
     // ---- store the tile's contiguous output block (transposed into the

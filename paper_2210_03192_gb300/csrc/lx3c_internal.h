@@ -101,6 +101,7 @@ struct ClassDesc {
   //   J[ao_a + A][ao_b + B] += wj * sum_{q,C} I[A][B][C] c[aux_ao[q] + C]
   // w = 2 (1 for a == b), wj = 1 (1/2 for a == b); J is symmetrised afterwards.
   int digest;
+  int dscr;                // digestion scratch (doubles): D block [nA*nB], then c [T][nC]
   long long ldD;           // row stride of D and J
   const double* D;
   const double* cvec;
@@ -208,6 +209,10 @@ struct LaunchShape {
   int T, G, mode;
   int smem_bytes;
 };
+// Places the DF-J digestion scratch (D block and the tile's c values) in the
+// stage region the final block does not occupy, or appends it when that region
+// is too small; updates d.dscr and d.smem_doubles.
+void set_digest_scratch(ClassDesc& d);
 LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit);
 void fill_layout(ClassDesc& d, const ClassTables& ct, const LaunchShape& s);
 

@@ -359,8 +359,11 @@ ClassTables build(int la, int lb, int lc, int bra_pure) {
 
   // ---------------- algorithmic flop counts (FMA = 2) ----------------
   double fp = 0;
-  fp += 32 + (lc > 0 ? 4.0 * (lc - 1) : 0.0);       // geometry, rsqrt, prefactor, factor powers
-  fp += 32 + 3.0 * Lab;                             // Boys (two degree-7 polynomials) and [00|0]^(m)
+  // geometry, rsqrt, prefactor, factor powers ((rho/gamma) PC only when VRR1 runs)
+  fp += 32 + (lc > 0 ? 4.0 * (lc - 1) : 0.0) - (Lab == 0 ? 3.0 : 0.0);
+  // Boys and [00|0]^(m): one degree-7 polynomial for F_L; the exp(-T)
+  // polynomial and the downward relation only when Lab > 0 (F_L..F_lc)
+  fp += Lab == 0 ? 16.0 : 32.0 + 3.0 * Lab;
   for (int e = 1; e <= Lab; ++e)
     for (int i = ct.vlev_start[e - 1]; i < ct.vlev_start[e]; ++i) fp += ((ct.vtab[i].z >> 20) & 0xF) ? 7 : 3;
   for (auto& w : ct.wtab) {
@@ -507,6 +510,19 @@ LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux,
   }
   if (!found) best.smem_bytes = -1;
   return best;
+}
+
+void set_digest_scratch(ClassDesc& d) {
+  const long long need = (long long)d.onA * d.onB + (long long)d.T * d.nC;
+  const bool out_in_x = d.OUT.base == d.V.base;
+  const long long free_base = out_in_x ? d.P.base : d.V.base;
+  const long long free_size = out_in_x ? (long long)d.V.base - d.P.base : (long long)d.smem_doubles - d.V.base;
+  if (need <= free_size) {
+    d.dscr = (int)free_base;
+  } else {
+    d.dscr = d.smem_doubles;
+    d.smem_doubles += (int)need;
+  }
 }
 
 void fill_layout(ClassDesc& d, const ClassTables& ct, const LaunchShape& sh) {
