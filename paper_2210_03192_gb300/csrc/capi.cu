@@ -109,7 +109,8 @@ lx3c_status device_class(DevState* s, const ClassTables& ct, DevClass** out) {
          o_gp = append(blob, ct.gptr), o_gt = append(blob, ct.gterm), o_gd = append(blob, ct.gdst),
          o_pal = append(blob, ct.pal), o_kp = append(blob, ct.kptr), o_ke = append(blob, ct.kent),
          o_h = append(blob, ct.htab), o_bap = append(blob, ct.baptr), o_bae = append(blob, ct.baent),
-         o_bbp = append(blob, ct.bbptr), o_bbe = append(blob, ct.bbent);
+         o_bbp = append(blob, ct.bbptr), o_bbe = append(blob, ct.bbent), o_ge = append(blob, ct.gell),
+         o_gs = append(blob, ct.gslice);
   DevClass dc;
   CUDA_TRY(cudaMalloc(&dc.blob, blob.size()));
   CUDA_TRY(cudaMemcpy(dc.blob, blob.data(), blob.size(), cudaMemcpyHostToDevice));
@@ -128,6 +129,8 @@ lx3c_status device_class(DevState* s, const ClassTables& ct, DevClass** out) {
   dc.baent = (const int2*)(b + o_bae);
   dc.bbptr = (const int*)(b + o_bbp);
   dc.bbent = (const int2*)(b + o_bbe);
+  dc.gell = (const unsigned*)(b + o_ge);
+  dc.gslice = (const int2*)(b + o_gs);
   auto r = s->classes.emplace(key, dc);
   *out = &r.first->second;
   return LX3C_OK;
@@ -168,6 +171,7 @@ int fill_class_desc(ClassDesc& d, const ClassTables& ct, const DevClass& dc, con
   d.nbA = ct.nbA; d.nbB = ct.nbB;
   d.vtab = dc.vtab; d.wtab = dc.wtab; d.atab = dc.atab; d.gptr = dc.gptr; d.gterm = dc.gterm;
   d.gdst = dc.gdst; d.pal = dc.pal; d.kptr = dc.kptr; d.kent = dc.kent; d.htab = dc.htab;
+  d.gell = dc.gell; d.gslice = dc.gslice;
   d.baptr = dc.baptr; d.baent = dc.baent; d.bbptr = dc.bbptr; d.bbent = dc.bbent;
   d.boys_tab = ds->boys_tab; d.boys_mid = ds->boys_mid; d.boys_cL = boys_large_const(d.L);
   fill_layout(d, ct, sh);

@@ -469,29 +469,54 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
         dec2(w, mode, fT, fX, t, r);
         if (t >= tv) continue;
         const int id = __ldg(d.gdst + r);
-        const int q0 = __ldg(d.gptr + id), q1 = __ldg(d.gptr + id + 1);
         double s = 0.0;
+        if (mode == 0) {
+          // lanes share the target: CSR row, broadcast loads
+          const int q0 = __ldg(d.gptr + id), q1 = __ldg(d.gptr + id + 1);
 #pragma unroll 4
-        for (int q = q0; q < q1; ++q) {
-          const unsigned e = __ldg(d.gterm + q);
-          s = fma(__ldg(d.pal + (e >> 20)), sm[BUF_T(d.P, e & 0xFFFFF, t)], s);
+          for (int q = q0; q < q1; ++q) {
+            const unsigned e = __ldg(d.gterm + q);
+            s = fma(__ldg(d.pal + (e >> 20)), sm[BUF_T(d.P, e & 0xFFFFF, t)], s);
+          }
+        } else {
+          // lanes take consecutive targets: sliced ELL, one coalesced line
+          // per term step and one trip count per slice
+          const int2 sl = __ldg(d.gslice + (r >> 5));
+          const unsigned* ge = d.gell + sl.x + (r & 31);
+#pragma unroll 4
+          for (int j = 0; j < sl.y; ++j) {
+            const unsigned e = __ldg(ge + 32 * j);
+            s = fma(__ldg(d.pal + (e >> 20)), sm[BUF_T(d.P, e & 0xFFFFF, t)], s);
+          }
         }
         sm[BUF_T(d.Gb, id, t)] = s;
       }
     }
     __syncthreads();
-    // ---- ket: Cartesian -> solid harmonic
+    // ---- ket: Cartesian -> solid harmonic.  With targets across lanes
+    // (mode 1) the items run C-major, so a warp's lanes share one C and with
+    // it the loop trip count (a warp instruction costs the same whatever the
+    // number of active lanes).
     {
-      FDiv fX, fC;
+      FDiv fX, fC, fR;
       const int nx = d.nkrow * d.nC;
       fX.init(nx);
       fC.init(d.nC);
+      fR.init(d.nkrow);
       const unsigned n = (unsigned)(T * nx);
       for (unsigned w = tid; w < n; w += kThreads) {
         int t, x;
         dec2(w, mode, fT, fX, t, x);
         if (t >= tv) continue;
-        const int row = (int)fC.div(x), C = x - row * d.nC;
+        int row, C;
+        if (mode == 0) {
+          row = (int)fC.div(x);
+          C = x - row * d.nC;
+        } else {
+          C = (int)fR.div(x);
+          row = x - C * d.nkrow;
+        }
+        x = row * d.nC + C;
         const int q0 = __ldg(d.kptr + C), q1 = __ldg(d.kptr + C + 1);
         double s = 0.0;
         for (int q = q0; q < q1; ++q) {
@@ -554,19 +579,32 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       cur = d.BA;
     }
     if (d.nbB) {
-      FDiv fX, fC, fB;
+      // items B-slowest in mode 1: a warp's lanes share B's trip count
+      FDiv fX, fC, fB, fAC;
       const int nx = d.nbB * d.nC;
-      const int nBs = d.nB;
+      const int nBs = d.nB, nAC = (d.nbB / d.nB) * d.nC;
       fX.init(nx);
       fC.init(d.nC);
       fB.init(nBs);
+      fAC.init(nAC);
       const unsigned n = (unsigned)(T * nx);
       for (unsigned w = tid; w < n; w += kThreads) {
         int t, x;
         dec2(w, mode, fT, fX, t, x);
         if (t >= tv) continue;
-        const int row = (int)fC.div(x), C = x - row * d.nC;
-        const int A = (int)fB.div(row), B = row - A * nBs;
+        int A, B, C;
+        if (mode == 0) {
+          const int row = (int)fC.div(x);
+          C = x - row * d.nC;
+          A = (int)fB.div(row);
+          B = row - A * nBs;
+        } else {
+          B = (int)fAC.div(x);
+          const int rem = x - B * nAC;
+          A = (int)fC.div(rem);
+          C = rem - A * d.nC;
+        }
+        x = (A * nBs + B) * d.nC + C;
         const int q0 = __ldg(d.bbptr + B), q1 = __ldg(d.bbptr + B + 1);
         double s;
         const int2 e0 = __ldg(d.bbent + q0);

@@ -71,6 +71,11 @@ struct ClassDesc {
   const unsigned* atab;    // accumulator -> vidx | widx<<16
   const int* gptr;         // gather CSR row pointers (by target id)
   const unsigned* gterm;   // gather terms: pidx | coef_id<<20
+  // the same terms as sliced ELL for targets across lanes: slice s = targets
+  // gdst[32s .. 32s+31], entry j of lane l at gell[gslice[s].x + 32 j + l]
+  // (padded to the slice's longest row with zero-coefficient terms)
+  const unsigned* gell;
+  const int2* gslice;
   const int* gdst;         // gather item r -> target id (items sorted by term count)
   const double* pal;       // coefficient palette
   const int* kptr;         // ket CSR by C
@@ -145,6 +150,8 @@ struct ClassTables {
   std::vector<unsigned> atab;
   std::vector<int> gptr, gdst;
   std::vector<unsigned> gterm;
+  std::vector<unsigned> gell;  // gather terms, sliced ELL (32 targets per slice, gdst order)
+  std::vector<int2> gslice;    // per slice {first entry, terms per target}
   std::vector<double> pal;
   std::vector<int> kptr;
   std::vector<int2> kent;
@@ -170,6 +177,8 @@ struct DevClass {
   const unsigned* atab;
   const int* gptr;
   const unsigned* gterm;
+  const unsigned* gell;
+  const int2* gslice;
   const int* gdst;
   const double* pal;
   const int* kptr;

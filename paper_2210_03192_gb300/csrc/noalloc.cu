@@ -181,14 +181,15 @@ extern "C" lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb
     return na_fail(LX3C_ENOTSUP, ex.what());
   }
   std::vector<char> blob;
-  size_t offs[2][14];
+  size_t offs[2][16];
   for (int o = 0; o < 1 + split; ++o) {
     const ClassTables& ct = *cts[o];
     size_t* f = offs[o];
     f[0] = put(blob, ct.vtab); f[1] = put(blob, ct.wtab); f[2] = put(blob, ct.atab); f[3] = put(blob, ct.gptr);
     f[4] = put(blob, ct.gterm); f[5] = put(blob, ct.gdst); f[6] = put(blob, ct.pal); f[7] = put(blob, ct.kptr);
     f[8] = put(blob, ct.kent); f[9] = put(blob, ct.htab); f[10] = put(blob, ct.baptr); f[11] = put(blob, ct.baent);
-    f[12] = put(blob, ct.bbptr); f[13] = put(blob, ct.bbent);
+    f[12] = put(blob, ct.bbptr); f[13] = put(blob, ct.bbent); f[14] = put(blob, ct.gell);
+    f[15] = put(blob, ct.gslice);
   }
   if (blob.size() > kTableBytes) return na_fail(LX3C_ENOTSUP, "class tables exceed the scratch table region");
   unsigned char* tb = base + kOffTables;
@@ -232,6 +233,7 @@ extern "C" lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb
     d.pal = (const double*)(tb + f[6]); d.kptr = (const int*)(tb + f[7]); d.kent = (const int2*)(tb + f[8]);
     d.htab = (const int4*)(tb + f[9]); d.baptr = (const int*)(tb + f[10]); d.baent = (const int2*)(tb + f[11]);
     d.bbptr = (const int*)(tb + f[12]); d.bbent = (const int2*)(tb + f[13]);
+    d.gell = (const unsigned*)(tb + f[14]); d.gslice = (const int2*)(tb + f[15]);
     d.boys_tab = (const double*)(base + kOffBoys);
     d.boys_mid = (const double*)(base + kOffBoysMid);
     d.boys_cL = boys_large_const(d.L);

@@ -316,6 +316,22 @@ ClassTables build(int la, int lb, int lc, int bra_pure) {
   std::stable_sort(ct.gdst.begin(), ct.gdst.end(), [&](int x, int y) {
     return (ct.gptr[x + 1] - ct.gptr[x]) > (ct.gptr[y + 1] - ct.gptr[y]);
   });
+  {
+    // sliced ELL copy: padding terms read accumulator 0 with coefficient 0
+    const unsigned pad = 0u | (pal_id(ct.pal, palids, 0.0) << 20);
+    for (int s0 = 0; s0 < ngt; s0 += 32) {
+      int mx = 0;
+      for (int l = s0; l < std::min(ngt, s0 + 32); ++l) mx = std::max(mx, ct.gptr[ct.gdst[l] + 1] - ct.gptr[ct.gdst[l]]);
+      ct.gslice.push_back(int2{(int)ct.gell.size(), mx});
+      for (int j = 0; j < mx; ++j)
+        for (int l = 0; l < 32; ++l) {
+          const int r = s0 + l;
+          const int id = r < ngt ? ct.gdst[r] : -1;
+          const bool has = id >= 0 && j < ct.gptr[id + 1] - ct.gptr[id];
+          ct.gell.push_back(has ? ct.gterm[ct.gptr[id] + j] : pad);
+        }
+    }
+  }
 
   // ---------------- ket transform ----------------
   auto Tc = solid_matrix(lc);
