@@ -122,7 +122,11 @@ void lx3c_plan_destroy(lx3c_plan* plan);
  * One-call host-buffer form of lx3c_eri3c_plan + lx3c_eri3c_execute: shell
  * tables, lists and the output are host memory; device memory is allocated
  * and freed inside the call, which synchronises `stream` before returning.
- * out_host receives npair*naux*nA*nB*nC doubles.
+ * out_host receives npair*naux*nA*nB*nC doubles (same layout as execute).
+ * The output is produced in pair-range chunks of about 512 MB that alternate
+ * between two device buffers; each chunk is copied to out_host on a second
+ * stream while the next is computed, so the device holds two chunks, not the
+ * whole output.  Page-locked out_host gives the full copy rate.
  */
 lx3c_status lx3c_eri3c_host(int64_t orb_nshell, const int32_t* orb_l, const int32_t* orb_k,
                             const double* orb_xyz, const double* orb_exps, const double* orb_coefs,

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -241,6 +242,7 @@ struct Launch {
   long long nsub = 0;
   int4* d_sub = nullptr;
   int* d_prim = nullptr;
+  std::vector<int> sub_pair;  // pair index of each sub-pair (ascending)
 };
 
 struct lx3c_plan {
@@ -356,6 +358,8 @@ lx3c_status make_launch(DevState* ds, lx3c_plan* p, int orient, const std::vecto
   Launch& L = p->L[orient];
   L.nsub = (long long)sub.size();
   if (L.nsub == 0) return LX3C_OK;
+  L.sub_pair.resize(sub.size());
+  for (size_t i = 0; i < sub.size(); ++i) L.sub_pair[i] = sub[i].x;
   const int l1 = orient ? p->lb : p->la, l2 = orient ? p->la : p->lb;
   const ClassTables* ct;
   try {
@@ -512,16 +516,64 @@ lx3c_status lx3c_eri3c_host(int64_t orb_nshell, const int32_t* orb_l, const int3
   if (!rc) rc = lx3c_eri3c_plan(&plan, orb, aux, pairs, npair, auxs, naux, bra_pure, stream);
   int64_t total = 0;
   if (!rc) rc = lx3c_plan_sizes(plan, nullptr, &total);
-  if (!rc) {
-    cudaError_t e = cudaMalloc(&d_out, (size_t)total * 8);
+  // Pair-range chunks of about 512 MB alternate between two device buffers;
+  // each finished chunk is copied to the host on a second stream while the
+  // next one is computed.
+  cudaStream_t cs = nullptr;
+  cudaEvent_t done[2] = {}, freed[2] = {};
+  const long long per_pair = plan ? plan->naux * plan->nblk : 0;
+  long long cp = 1;
+  if (!rc && total > 0) {
+    cp = std::max(1LL, std::min<long long>(npair, (512LL << 20) / 8 / std::max(1LL, per_pair)));
+    cudaError_t e = cudaMalloc(&d_out, (size_t)(2 * cp * per_pair) * 8);
     if (e != cudaSuccess) rc = fail(LX3C_ENOMEM, "eri3c_host: device output allocation failed");
   }
-  if (!rc) rc = lx3c_eri3c_execute(plan, d_out, stream);
-  if (!rc) {
-    cudaError_t e = cudaMemcpyAsync(out_host, d_out, (size_t)total * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (!rc && total > 0) {
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&freed[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = launch_pair_precompute(plan->orb->dev(), plan->d_pairs, plan->npair, plan->Ka, plan->Kb,
+                                                     plan->d_pairrec, plan->d_pairab, st);
+    if (e == cudaSuccess) e = launch_aux_precompute(plan->aux->dev(), plan->d_auxs, plan->naux, plan->Kc, plan->d_auxrec,
+                                                    plan->d_auxc, st);
+    int c = 0;
+    for (long long p0 = 0; p0 < npair && e == cudaSuccess; p0 += cp, ++c) {
+      const long long p1 = std::min<long long>(npair, p0 + cp);
+      const int b = c & 1;
+      double* buf = d_out + (size_t)b * cp * per_pair;
+      if (c >= 2) e = cudaStreamWaitEvent(st, freed[b], 0);
+      for (auto& L : plan->L) {
+        if (!L.nsub || e != cudaSuccess) continue;
+        const long long s0 = std::lower_bound(L.sub_pair.begin(), L.sub_pair.end(), (int)p0) - L.sub_pair.begin();
+        const long long s1 = std::lower_bound(L.sub_pair.begin(), L.sub_pair.end(), (int)p1) - L.sub_pair.begin();
+        if (s1 <= s0) continue;
+        ClassDesc d = L.desc;
+        d.out = buf;
+        d.out_pair0 = p0;
+        d.subpairs = L.d_sub + s0;
+        d.nsub = s1 - s0;
+        d.ntiles = d.nsub * d.ntile_aux;
+        e = launch_eri3c(d, (int)std::min<long long>(L.grid, d.ntiles), st);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(done[b], st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, done[b], 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_host + p0 * per_pair, buf, (size_t)((p1 - p0) * per_pair) * 8, cudaMemcpyDeviceToHost, cs);
+      if (e == cudaSuccess) e = cudaEventRecord(freed[b], cs);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(cs);
+    if (e == cudaSuccess) e = e2;
+    e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) rc = fail(LX3C_ECUDA, std::string("eri3c_host: ") + cudaGetErrorString(e));
   }
+  for (int b = 0; b < 2; ++b) {
+    if (done[b]) cudaEventDestroy(done[b]);
+    if (freed[b]) cudaEventDestroy(freed[b]);
+  }
+  if (cs) cudaStreamDestroy(cs);
   cudaFree(d_out);
   lx3c_plan_destroy(plan);
   lx3c_basis_destroy(orb);

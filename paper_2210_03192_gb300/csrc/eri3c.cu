@@ -730,7 +730,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       fB.init(d.nblk);
       fBC.init(d.onB * d.nC);
       fC.init(d.nC);
-      double* o = d.out + (pair * d.naux + aux0) * (long long)d.nblk;
+      double* o = d.out + ((pair - d.out_pair0) * d.naux + aux0) * (long long)d.nblk;
       const unsigned n = (unsigned)(tv * d.nblk);
       for (unsigned w = tid; w < n; w += kThreads) {
         const unsigned t = fB.div(w);

@@ -98,6 +98,7 @@ struct ClassDesc {
   const double* boys_mid;  // [kBoysNInt]
   double boys_cL;          // Gamma(L+1/2)/2 for the large-T branch
   double* out;
+  long long out_pair0;     // pair index of out's first block (0 unless the output is chunked)
   // optional explicit tile table {sub-pair, first ket-list entry, ket count, 0};
   // when null, tiles are (sub-pair, T consecutive ket shells) over all naux
   const int4* tiles;

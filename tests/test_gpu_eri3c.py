@@ -78,6 +78,18 @@ def test_host_path_matches_device(lx):
     np.testing.assert_array_equal(g, h)
 
 
+def test_host_path_chunked(lx):
+    """Host path over several ~512 MB output chunks (two device buffers, copies
+    overlapped with compute) against the device path, bit for bit; random
+    exponents give pairs split between both orientations at chunk edges."""
+    p = W.class_problem(4, 4, 6, 300, 512, 1, 1, 1, box=20.0, exp_lo=0.05, exp_hi=1e4, seed=77)
+    g = run(lx, p)
+    h = torch.empty(g.size, dtype=torch.float64, pin_memory=True).numpy().reshape(g.shape)
+    lx.eri3c_host(p.orb, p.aux, p.pairs, p.auxs, out=h)
+    assert h.nbytes > 2 * (512 << 20)
+    np.testing.assert_array_equal(g, h)
+
+
 def test_boys_device(lx):
     """Device Boys evaluator against the oracle's extended-precision Boys function."""
     rng = np.random.default_rng(3)
