@@ -34,6 +34,13 @@ sys.path.insert(0, ROOT)
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 FP64_PEAK_MEASURED = 1191.9
 
+# DRAM traffic of the (gg|i) K_ab=6 class per pair (512 ket shells, both oriented
+# launches), from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
+# on 64 pairs x 512 ket shells (59,150,592 + 208,663,552 bytes), scaled by pairs;
+# the integral blocks written are 4,312,448 bytes per pair, so traffic is 0.97x the
+# algorithmic bytes (no re-reads; the B-oriented launch reads back blocks it adds to).
+GGI_K6_DRAM_BYTES_PER_PAIR = (59150592 + 208663552) / 64
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -203,7 +210,11 @@ def run_ours(args, rank, world, dist):
     res = dict(ms=ms, total_int=total_int, total_flops=total_flops, table=table, clocks=clk, setup_s=setup_s,
                launches=launches_per_step * args.steps,
                roofline=dict(bound="alu", achieved=round(ach, 2), peak=round(FP64_PEAK_GFLOPS, 1), unit="GFLOP/s",
-                             frac=round(ach / FP64_PEAK_GFLOPS, 4), traffic=None,
+                             frac=round(ach / FP64_PEAK_GFLOPS, 4),
+                             traffic=(round(GGI_K6_DRAM_BYTES_PER_PAIR * args.npair)
+                                      if plans[dom]["cls"] == (4, 4, 6, 6) and args.naux == 512 and not args.product_k
+                                      else None),
+                             traffic_source="ncu dram bytes, both launches, 64 pairs x 512 kets, scaled by pairs",
                              kernel="eri3c_kernel class (%d%d|%d) K_ab=%d" % plans[dom]["cls"],
                              peak_source="152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit counts); "
                                          "measured DFMA microbenchmark %.1f" % FP64_PEAK_MEASURED,
