@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--naux", type=int, default=512)
     ap.add_argument("--product-k", action="store_true", help="read K_ab as (K_a, K_b) = (K_ab, 1)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-hints", action="store_true", help="ignore the package's tuned tile-shape hints")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--per-class-out", default=None, help="write the per-class table to this JSON file")
@@ -150,6 +151,9 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(dev)
     classes = class_list(args)
     t0 = time.time()
+    args.hints = 0
+    if not args.no_hints and os.path.exists(lx.HINTS_GB300):
+        args.hints = lx.load_shape_hints(lx.HINTS_GB300)
     plans = build_plans(classes, args, rank)
     maxtot = max(p["plan"].total for p in plans)
     out = torch.empty(maxtot, dtype=torch.float64, device=dev)
@@ -330,7 +334,9 @@ def main():
                                                                                                    args.naux),
                     classes=len(classes), integrals_per_step=res["total_int"] // (args.steps * world),
                     l2="each step writes the whole sweep's blocks (TB-scale, far above the 129 MB L2); no flush",
-                    parallelism="dp%d (independent sweeps per rank)" % world),
+                    parallelism="dp%d (independent sweeps per rank)" % world,
+                    tile_shapes=("planner default + %d tuned hints (shape_hints_gb300.txt)" % getattr(args, "hints", 0)
+                                 if getattr(args, "hints", 0) else "planner default")),
         roofline=res["roofline"], cpu_baseline=cpu, clocks=res["clocks"], gpu_launches=res["launches"],
         fp64_tflops_sweep=round(res["total_flops"] / (res["ms"] / 1e3) / 1e12, 4),
         l3_roofline_frac=res["l3_frac"],

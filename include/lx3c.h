@@ -150,6 +150,23 @@ lx3c_status lx3c_boys(const double* T, int64_t n, int mmax, double* out, void* s
  */
 lx3c_status lx3c_class_flops(int la, int lb, int lc, int Kab, int Kc, int bra_pure, double* flops);
 
+/*
+ * Launch-shape tuning (not in the paper).  The planner sizes a tile (triples
+ * per tile T, primitive chunk G) for two CTAs per SM by default.
+ * lx3c_shape_hint makes every later plan of class (la, lb | lc) -- as the
+ * planner orients it, so (lb, la | lc) for the B-oriented launch -- with kab
+ * primitive pairs in its largest sub-pair and kc ket primitives size its tile
+ * for ctas_per_sm CTAs per SM instead (1..3; 0 removes the hint).
+ * Process-wide, thread-safe; plans made before the call keep their shapes.
+ * lx3c_shape_query: out[4] = {T, G, lane mode, dynamic shared memory bytes}
+ * of that class for naux ket shells at ctas_per_sm CTAs per SM (0: the shape
+ * the planner picks now, hints included); host only, no device needed.
+ * Both return LX3C_EINVAL for arguments out of range.
+ */
+lx3c_status lx3c_shape_hint(int la, int lb, int lc, int bra_pure, int kab, int kc, int ctas_per_sm);
+lx3c_status lx3c_shape_query(int la, int lb, int lc, int bra_pure, int kab, int kc, int64_t naux, int ctas_per_sm,
+                             int32_t* out);
+
 /* Library's solid-harmonic matrix for shell l: out[(m+l)*ncart(l) + c]. */
 lx3c_status lx3c_solid_harmonics(int l, double* out);
 

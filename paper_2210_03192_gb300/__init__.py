@@ -15,6 +15,7 @@ Main entry points:
   class_flops(la, lb, lc, Kab, Kc, bra_pure)   algorithmic FP64 flops per triple
 """
 import ctypes
+import os
 
 import numpy as np
 
@@ -331,6 +332,38 @@ def boys(T, mmax, stream=None):
     check(_lib.load().lx3c_boys(ctypes.c_void_p(T.data_ptr()), T.numel(), int(mmax), ctypes.c_void_p(out.data_ptr()),
                                 _stream_handle(stream)), "lx3c_boys")
     return out
+
+
+def shape_hint(la, lb, lc, kab, kc=1, ctas_per_sm=2, bra_pure=True):
+    """Size later plans of class (la, lb | lc) with kab x kc primitives for
+    ctas_per_sm CTAs per SM (lx3c_shape_hint; 0 removes the hint)."""
+    check(_lib.load().lx3c_shape_hint(la, lb, lc, int(bool(bra_pure)), kab, kc, ctas_per_sm), "lx3c_shape_hint")
+
+
+def shape_query(la, lb, lc, kab, kc=1, naux=512, ctas_per_sm=0, bra_pure=True):
+    """(T, G, mode, smem bytes) the planner gives the class (lx3c_shape_query)."""
+    out = np.zeros(4, np.int32)
+    check(_lib.load().lx3c_shape_query(la, lb, lc, int(bool(bra_pure)), kab, kc, int(naux), ctas_per_sm, ptr(out)),
+          "lx3c_shape_query")
+    return tuple(int(x) for x in out)
+
+
+HINTS_GB300 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "shape_hints_gb300.txt")
+
+
+def load_shape_hints(path=HINTS_GB300):
+    """Apply a tuned hints file ("la lb lc bra_pure kab kc ctas_per_sm" per line,
+    '#' comments); returns the number of hints applied."""
+    n = 0
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if not line:
+                continue
+            la, lb, lc, pure, kab, kc, ctas = (int(x) for x in line)
+            shape_hint(la, lb, lc, kab, kc, ctas, bool(pure))
+            n += 1
+    return n
 
 
 def class_flops(la, lb, lc, Kab, Kc=1, bra_pure=True):

@@ -591,6 +591,31 @@ lx3c_status lx3c_boys(const double* T, int64_t n, int mmax, double* out, void* s
   return LX3C_OK;
 }
 
+lx3c_status lx3c_shape_hint(int la, int lb, int lc, int bra_pure, int kab, int kc, int ctas_per_sm) {
+  if (la < 0 || lb < 0 || lc < 0 || la > LX3C_LMAX_ORB + 1 || lb > LX3C_LMAX_ORB + 1 || lc > LX3C_LMAX_AUX ||
+      kab < 1 || kc < 1 || ctas_per_sm < 0 || ctas_per_sm > 3)
+    return fail(LX3C_EINVAL, "shape_hint: bad argument");
+  set_shape_hint(la, lb, lc, bra_pure, kab, kc, ctas_per_sm);
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_shape_query(int la, int lb, int lc, int bra_pure, int kab, int kc, int64_t naux, int ctas_per_sm,
+                             int32_t* out) {
+  if (!out || la < 0 || lb < 0 || lc < 0 || la > LX3C_LMAX_ORB + 1 || lb > LX3C_LMAX_ORB + 1 ||
+      lc > LX3C_LMAX_AUX || kab < 1 || kc < 1 || naux < 1 || ctas_per_sm < 0 || ctas_per_sm > 3)
+    return fail(LX3C_EINVAL, "shape_query: bad argument");
+  try {
+    const ClassTables& ct = class_tables(la, lb, lc, bra_pure ? 1 : 0);
+    const int smem = 233472;  // shared memory per SM of the target (GB300)
+    LaunchShape sh = ctas_per_sm ? choose_shape_for(ct, kab, kc, naux, smem, ctas_per_sm)
+                                 : choose_shape(ct, kab, kc, naux, smem);
+    out[0] = sh.T; out[1] = sh.G; out[2] = sh.mode; out[3] = sh.smem_bytes;
+  } catch (std::exception& e) {
+    return fail(LX3C_ENOTSUP, e.what());
+  }
+  return LX3C_OK;
+}
+
 lx3c_status lx3c_class_flops(int la, int lb, int lc, int Kab, int Kc, int bra_pure, double* flops) {
   if (!flops || la < 0 || lb < 0 || lc < 0 || la > LX3C_LMAX_ORB || lb > LX3C_LMAX_ORB || lc > LX3C_LMAX_AUX ||
       Kab < 1 || Kc < 1)

@@ -224,6 +224,8 @@ struct LaunchShape {
 // is too small; updates d.dscr and d.smem_doubles.
 void set_digest_scratch(ClassDesc& d);
 LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit);
+LaunchShape choose_shape_for(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit, int ctas);
+void set_shape_hint(int la, int lb, int lc, int bra_pure, int Kab, int Kc, int ctas);
 void fill_layout(ClassDesc& d, const ClassTables& ct, const LaunchShape& s);
 
 // Orientation split of one pair's primitive pairs (capi.cu).

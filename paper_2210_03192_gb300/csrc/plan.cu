@@ -492,15 +492,34 @@ void buffer_sizes(const ClassTables& ct, int Kab, int Kc, int T, int G, int mode
 
 }  // namespace
 
-LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit) {
+namespace {
+std::mutex g_hint_mu;
+std::map<std::tuple<int, int, int, int, int, int>, int> g_hints;  // (la, lb, lc, pure, Kab, Kc) -> CTAs/SM
+}  // namespace
+
+void set_shape_hint(int la, int lb, int lc, int bra_pure, int Kab, int Kc, int ctas) {
+  std::lock_guard<std::mutex> lk(g_hint_mu);
+  auto key = std::make_tuple(la, lb, lc, bra_pure ? 1 : 0, Kab, Kc);
+  if (ctas <= 0) g_hints.erase(key); else g_hints[key] = ctas;
+}
+
+int shape_hint(const ClassTables& ct, int Kab, int Kc) {
+  std::lock_guard<std::mutex> lk(g_hint_mu);
+  auto it = g_hints.find(std::make_tuple(ct.la, ct.lb, ct.lc, ct.bra_pure ? 1 : 0, Kab, Kc));
+  return it == g_hints.end() ? 0 : it->second;
+}
+
+// Largest T (then largest balanced G) whose tile fits `ctas` CTAs per SM,
+// falling back to fewer CTAs per SM when nothing fits.
+LaunchShape choose_shape_for(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit, int ctas) {
   const int K = Kab * Kc;
-  const long long budget2 = (smem_limit / 2 - 1024) / 8;  // two CTAs per SM
-  const long long budget1 = (smem_limit - 1024) / 8;
+  std::vector<long long> budgets;
+  for (int c = std::max(1, ctas); c >= 1; --c) budgets.push_back((smem_limit / c - 1024) / 8);
   LaunchShape best{1, 1, 1, 0};
   Sizes s;
   int Ts[] = {512, 256, 128, 64, 32, 16, 8, 4, 2, 1};
   bool found = false;
-  for (long long budget : {budget2, budget1}) {
+  for (long long budget : budgets) {
     for (int T : Ts) {
       if (T > 1 && T > 2 * naux && T != 1) continue;
       int mode = T >= 32 ? 0 : 1;
@@ -526,6 +545,13 @@ LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux,
   }
   if (!found) best.smem_bytes = -1;
   return best;
+}
+
+// The planner's shape: two CTAs per SM unless a tuned hint for this class,
+// contraction and ket contraction says otherwise.
+LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit) {
+  const int h = shape_hint(ct, Kab, Kc);
+  return choose_shape_for(ct, Kab, Kc, naux, smem_limit, h > 0 ? h : 2);
 }
 
 void set_digest_scratch(ClassDesc& d) {

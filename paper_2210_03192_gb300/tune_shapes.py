@@ -1,0 +1,79 @@
+"""Tune the planner's tile shape per class on the GPU at hand and write a hints
+file for load_shape_hints().
+
+For every (la, lb <= 4 | lc <= 6, K_ab in {1, 3, 6}) class of the per-class
+sweep recipe (workloads.config2_class, reduced to --npair pairs x 512 ket
+shells), the plan is built with its tiles sized for 1, 2 and 3 CTAs per SM
+(both oriented classes hinted alike) and timed with CUDA events (best of
+--reps executes after one warm-up).  A class gets a hint line when its best
+target beats the default (2 CTAs per SM) by more than --margin.
+
+    python -m paper_2210_03192_gb300.tune_shapes [--out FILE] [--npair N]
+"""
+import argparse
+import sys
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=None, help="hints file (default: the package's shape_hints_gb300.txt)")
+    ap.add_argument("--npair", type=int, default=1024)
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--margin", type=float, default=0.03)
+    ap.add_argument("--classes", nargs="*", default=None, help="subset la,lb,lc,Kab")
+    args = ap.parse_args(argv)
+    import torch
+    import paper_2210_03192_gb300 as lx
+    from paper_2210_03192_gb300 import workloads as W
+
+    classes = W.CONFIG2_CLASSES
+    if args.classes:
+        classes = [tuple(int(x) for x in c.split(",")) for c in args.classes]
+    lines, t0 = [], time.time()
+    for (la, lb, lc, K) in classes:
+        kab = K * K
+        p = W.config2_class(la, lb, lc, K, npair=args.npair, naux=512)
+        times = {}
+        for ctas in (2, 3, 1):
+            lx.shape_hint(la, lb, lc, kab, 1, ctas)
+            lx.shape_hint(lb, la, lc, kab, 1, ctas)
+            plan = lx.Eri3cPlan(p.orb, p.aux, p.pairs, p.auxs)
+            out = plan.execute()
+            best = float("inf")
+            for _ in range(args.reps):
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                plan.execute(out)
+                e.record()
+                torch.cuda.synchronize()
+                best = min(best, s.elapsed_time(e))
+            times[ctas] = best
+            del plan, out
+        lx.shape_hint(la, lb, lc, kab, 1, 0)
+        lx.shape_hint(lb, la, lc, kab, 1, 0)
+        win = min(times, key=times.get)
+        if win != 2 and times[win] < (1.0 - args.margin) * times[2]:
+            lines.append((la, lb, lc, kab, win, times[2], times[win]))
+            if lb != la:
+                lines.append((lb, la, lc, kab, win, times[2], times[win]))
+    best_line = {}
+    for ln in lines:  # (la,lb) and (lb,la) sweep classes hint the same pair of tables: keep the larger gain
+        key = ln[:4]
+        if key not in best_line or ln[6] / ln[5] < best_line[key][6] / best_line[key][5]:
+            best_line[key] = ln
+    lines = sorted(best_line.values())
+    path = args.out or lx.HINTS_GB300
+    with open(path, "w") as f:
+        f.write("# Tile-shape hints for lx3c (load_shape_hints): la lb lc bra_pure kab kc ctas_per_sm\n")
+        f.write("# written by paper_2210_03192_gb300/tune_shapes.py on %s, %d pairs x 512 ket shells per class;\n"
+                % (torch.cuda.get_device_name(0), args.npair))
+        f.write("# trailing comment: ms at 2 CTAs/SM -> ms at the hinted target\n")
+        for (a, b, c, kab, ctas, t2, tw) in lines:
+            f.write("%d %d %d 1 %d 1 %d  # %.3f -> %.3f\n" % (a, b, c, kab, ctas, t2, tw))
+    print("tuned %d classes in %.0f s, %d hint lines -> %s" % (len(classes), time.time() - t0, len(lines), path))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

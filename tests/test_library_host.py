@@ -117,3 +117,41 @@ def test_device_calls_fail_loudly_without_gpu():
         pytest.skip("GPU present")
     with pytest.raises(lx.LibraryError):
         lx.boys(torch.zeros(3, dtype=torch.float64), 4)
+
+
+def test_shape_query_budgets_and_hints(tmp_path):
+    """Planner shapes fit their CTAs-per-SM budget; a hint switches the default
+    shape of exactly its class; a hints file applies and removes cleanly."""
+    import paper_2210_03192_gb300 as lx
+    smem = 233472
+    for (la, lb, lc, kab) in [(4, 4, 6, 36), (4, 4, 1, 36), (2, 2, 2, 1), (0, 0, 0, 9), (3, 2, 5, 9)]:
+        for ctas in (1, 2, 3):
+            T, G, mode, sb = lx.shape_query(la, lb, lc, kab, 1, 512, ctas)
+            assert T >= 1 and 1 <= G <= min(kab, 8) and mode == (0 if T >= 32 else 1)
+            # fits the budget, or is the fallback of a smaller CTA count
+            assert sb <= smem - 1024
+            if sb > smem // ctas - 1024:
+                assert lx.shape_query(la, lb, lc, kab, 1, 512, ctas) == lx.shape_query(la, lb, lc, kab, 1, 512, ctas - 1)
+        default = lx.shape_query(la, lb, lc, kab, 1, 512, 0)
+        assert default == lx.shape_query(la, lb, lc, kab, 1, 512, 2)
+    three = lx.shape_query(4, 4, 1, 36, 1, 512, 3)
+    lx.shape_hint(4, 4, 1, 36, 1, 3)
+    try:
+        assert lx.shape_query(4, 4, 1, 36, 1, 512, 0) == three
+        assert lx.shape_query(4, 4, 1, 9, 1, 512, 0) == lx.shape_query(4, 4, 1, 9, 1, 512, 2)  # other kab untouched
+    finally:
+        lx.shape_hint(4, 4, 1, 36, 1, 0)
+    assert lx.shape_query(4, 4, 1, 36, 1, 512, 0) == lx.shape_query(4, 4, 1, 36, 1, 512, 2)
+    f = tmp_path / "hints.txt"
+    f.write_text("# la lb lc pure kab kc ctas\n4 4 1 1 36 1 3\n2 2 2 1 1 1 1\n")
+    assert lx.load_shape_hints(str(f)) == 2
+    try:
+        assert lx.shape_query(4, 4, 1, 36, 1, 512, 0) == three
+        assert lx.shape_query(2, 2, 2, 1, 1, 512, 0) == lx.shape_query(2, 2, 2, 1, 1, 512, 1)
+    finally:
+        lx.shape_hint(4, 4, 1, 36, 1, 0)
+        lx.shape_hint(2, 2, 2, 1, 1, 0)
+    with pytest.raises(lx.LibraryError):
+        lx.shape_hint(4, 4, 1, 36, 1, 4)
+    with pytest.raises(lx.LibraryError):
+        lx.shape_query(9, 4, 1, 36, 1, 512, 2)
