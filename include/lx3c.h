@@ -126,7 +126,10 @@ void lx3c_plan_destroy(lx3c_plan* plan);
  * The output is produced in pair-range chunks of about 512 MB that alternate
  * between two device buffers; each chunk is copied to out_host on a second
  * stream while the next is computed, so the device holds two chunks, not the
- * whole output.  Page-locked out_host gives the full copy rate.
+ * whole output.  The two buffers (at most ~1 GB, or two pairs' blocks if
+ * larger), the copy stream and its events are made on the first call and
+ * kept per device for later calls; concurrent calls on one device take turns.
+ * Page-locked out_host gives the full copy rate.
  */
 lx3c_status lx3c_eri3c_host(int64_t orb_nshell, const int32_t* orb_l, const int32_t* orb_k,
                             const double* orb_xyz, const double* orb_exps, const double* orb_coefs,

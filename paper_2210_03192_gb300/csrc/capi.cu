@@ -62,6 +62,14 @@ struct lx3c::DevState {
   int nsm = 0;
   int smem_per_sm = 0;
   std::map<std::tuple<int, int, int, int>, DevClass> classes;
+  // host-buffer path (lx3c_eri3c_host): the two output chunk buffers (grown,
+  // never shrunk), the copy stream and its events, made on first use and kept;
+  // calls on one device take turns on host_mu
+  std::mutex host_mu;
+  double* host_buf = nullptr;
+  size_t host_cap = 0;  // doubles
+  cudaStream_t host_cs = nullptr;
+  cudaEvent_t host_done[2] = {}, host_freed[2] = {};
 };
 
 namespace {
@@ -518,22 +526,38 @@ lx3c_status lx3c_eri3c_host(int64_t orb_nshell, const int32_t* orb_l, const int3
   if (!rc) rc = lx3c_plan_sizes(plan, nullptr, &total);
   // Pair-range chunks of about 512 MB alternate between two device buffers;
   // each finished chunk is copied to the host on a second stream while the
-  // next one is computed.
+  // next one is computed.  Buffers, stream and events persist per device.
+  DevState* ds = nullptr;
+  if (!rc) rc = device_state(&ds);
+  std::unique_lock<std::mutex> hl;
+  if (ds) hl = std::unique_lock<std::mutex>(ds->host_mu);
   cudaStream_t cs = nullptr;
-  cudaEvent_t done[2] = {}, freed[2] = {};
+  cudaEvent_t* done = ds ? ds->host_done : nullptr;
+  cudaEvent_t* freed = ds ? ds->host_freed : nullptr;
   const long long per_pair = plan ? plan->naux * plan->nblk : 0;
   long long cp = 1;
   if (!rc && total > 0) {
     cp = std::max(1LL, std::min<long long>(npair, (512LL << 20) / 8 / std::max(1LL, per_pair)));
-    cudaError_t e = cudaMalloc(&d_out, (size_t)(2 * cp * per_pair) * 8);
+    const size_t need = (size_t)(2 * cp * per_pair);
+    cudaError_t e = cudaSuccess;
+    if (ds->host_cap < need) {
+      cudaFree(ds->host_buf);
+      ds->host_buf = nullptr;
+      ds->host_cap = 0;
+      e = cudaMalloc(&ds->host_buf, need * 8);
+      if (e == cudaSuccess) ds->host_cap = need;
+    }
     if (e != cudaSuccess) rc = fail(LX3C_ENOMEM, "eri3c_host: device output allocation failed");
+    d_out = ds->host_buf;
   }
   if (!rc && total > 0) {
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    cudaError_t e = cudaSuccess;
+    if (!ds->host_cs) e = cudaStreamCreateWithFlags(&ds->host_cs, cudaStreamNonBlocking);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-      e = cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&freed[b], cudaEventDisableTiming);
+      if (!done[b]) e = cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
+      if (e == cudaSuccess && !freed[b]) e = cudaEventCreateWithFlags(&freed[b], cudaEventDisableTiming);
     }
+    cs = ds->host_cs;
     if (e == cudaSuccess) e = launch_pair_precompute(plan->orb->dev(), plan->d_pairs, plan->npair, plan->Ka, plan->Kb,
                                                      plan->d_pairrec, plan->d_pairab, st);
     if (e == cudaSuccess) e = launch_aux_precompute(plan->aux->dev(), plan->d_auxs, plan->naux, plan->Kc, plan->d_auxrec,
@@ -569,12 +593,7 @@ lx3c_status lx3c_eri3c_host(int64_t orb_nshell, const int32_t* orb_l, const int3
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) rc = fail(LX3C_ECUDA, std::string("eri3c_host: ") + cudaGetErrorString(e));
   }
-  for (int b = 0; b < 2; ++b) {
-    if (done[b]) cudaEventDestroy(done[b]);
-    if (freed[b]) cudaEventDestroy(freed[b]);
-  }
-  if (cs) cudaStreamDestroy(cs);
-  cudaFree(d_out);
+
   lx3c_plan_destroy(plan);
   lx3c_basis_destroy(orb);
   lx3c_basis_destroy(aux);
