@@ -64,7 +64,7 @@ def class_list(args):
     from paper_2210_03192_gb300 import workloads as W
     if args.classes:
         return [tuple(int(x) for x in c.split(",")) for c in args.classes]
-    return list(W.CONFIG2_CLASSES)
+    return list(W.SWEEP_CLASSES)
 
 
 def nint(la, lb, lc):
@@ -131,7 +131,7 @@ def build_plans(classes, args, rank):
     from paper_2210_03192_gb300 import workloads as W
     plans = []
     for (la, lb, lc, K) in classes:
-        p = W.config2_class(la, lb, lc, K, args.npair, args.naux, product_reading=args.product_k)
+        p = W.sweep_class(la, lb, lc, K, args.npair, args.naux, product_reading=args.product_k)
         if rank:
             # weak scaling: every rank evaluates a sweep of its own synthetic shells
             p = W.class_problem(la, lb, lc, args.npair, args.naux, *((K, 1) if args.product_k else (K, K)), 1,
@@ -265,7 +265,7 @@ def oracle_sample(classes, args, seconds):
     import oracle
     from paper_2210_03192_gb300 import workloads as W
     oracle.build()
-    probs = [W.config2_class(la, lb, lc, K, 64, 64, product_reading=args.product_k) for (la, lb, lc, K) in classes]
+    probs = [W.sweep_class(la, lb, lc, K, 64, 64, product_reading=args.product_k) for (la, lb, lc, K) in classes]
     npr = 1
     while True:
         t0 = time.perf_counter()
@@ -293,7 +293,7 @@ def run_reference(args, rank, world):
     line = dict(metric="3c-ERI Gints/s FP64 per (La,Lb,Lc,K)", value=v, unit="Gints/s", n_gpus=world,
                 steps=args.steps, warmup=args.warmup, ms_per_step=round(1000 * res[-1]["seconds"], 2),
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-                data="synthetic (config-2 recipe, seeded)", impl="reference",
+                data="synthetic (per-class sweep recipe, seeded)", impl="reference",
                 config=dict(workload="per-class sweep (la,lb<=4|lc<=6), K_ab in {1,3,6}, all-pure; oracle sample",
                             classes=len(classes)),
                 cpu_baseline=dict(value=v, unit="Gints/s", cores=res[-1]["cores"], kind="oracle",
@@ -329,7 +329,7 @@ def main():
         metric="3c-ERI Gints/s FP64 per (La,Lb,Lc,K)", value=round(value, 4), unit="Gints/s", n_gpus=world,
         steps=args.steps, warmup=args.warmup, ms_per_step=round(res["ms"] / args.steps, 2),
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-        data="synthetic (config-2 recipe, seeded; no public dataset)",
+        data="synthetic (per-class sweep recipe, seeded; no public dataset)",
         config=dict(workload="per-class sweep: every (la,lb<=4|lc<=6) class, K_ab in {1,3,6} (K_a=K_b=K_ab, K_c=1), "
                              "%d pairs x %d aux shells per class, all-pure, blocks written to HBM" % (args.npair,
                                                                                                    args.naux),

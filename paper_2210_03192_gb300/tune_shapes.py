@@ -2,7 +2,7 @@
 file for load_shape_hints().
 
 For every (la, lb <= 4 | lc <= 6, K_ab in {1, 3, 6}) class of the per-class
-sweep recipe (workloads.config2_class, reduced to --npair pairs x 512 ket
+sweep recipe (workloads.sweep_class, reduced to --npair pairs x 512 ket
 shells), the plan is built with its tiles sized for 1, 2 and 3 CTAs per SM
 (both oriented classes hinted alike) and timed with CUDA events (best of
 --reps executes after one warm-up).  A class gets a hint line when its best
@@ -27,13 +27,13 @@ def main(argv=None):
     import paper_2210_03192_gb300 as lx
     from paper_2210_03192_gb300 import workloads as W
 
-    classes = W.CONFIG2_CLASSES
+    classes = W.SWEEP_CLASSES
     if args.classes:
         classes = [tuple(int(x) for x in c.split(",")) for c in args.classes]
     lines, t0 = [], time.time()
     for (la, lb, lc, K) in classes:
         kab = K * K
-        p = W.config2_class(la, lb, lc, K, npair=args.npair, naux=512)
+        p = W.sweep_class(la, lb, lc, K, npair=args.npair, naux=512)
         times = {}
         for ctas in (2, 3, 1):
             lx.shape_hint(la, lb, lc, kab, 1, ctas)

@@ -123,13 +123,13 @@ def class_problem(la, lb, lc, npair, naux, Ka=1, Kb=1, Kc=1, box=10.0, exp_lo=0.
     return ClassProblem(la, lb, lc, orb, c, pairs, np.arange(naux, dtype=np.int32))
 
 
-def config1():
+def ppd_64x32():
     """(pp|d), K=1: 64 pairs x 32 aux shells; centres in a 10-bohr cube,
     exponents log-uniform in [0.1, 100], coefficients uniform in [0.1, 1]."""
     return class_problem(1, 1, 2, 64, 32, 1, 1, 1, box=10.0, exp_lo=0.1, exp_hi=100.0, seed=SEED_BASE + 0)
 
 
-def config2_class(la, lb, lc, Kab, npair=4096, naux=512, product_reading=False):
+def sweep_class(la, lb, lc, Kab, npair=4096, naux=512, product_reading=False):
     """Per-class sweep member: 4096 pairs x 512 aux shells, centres in a 20-bohr
     cube, exponents log-uniform in [0.05, 1e4], K_c = 1.
 
@@ -140,7 +140,7 @@ def config2_class(la, lb, lc, Kab, npair=4096, naux=512, product_reading=False):
     return class_problem(la, lb, lc, npair, naux, Ka, Kb, 1, box=20.0, exp_lo=0.05, exp_hi=1.0e4, seed=seed)
 
 
-CONFIG2_CLASSES = [(la, lb, lc, K) for la in range(5) for lb in range(5) for lc in range(7) for K in (1, 3, 6)]
+SWEEP_CLASSES = [(la, lb, lc, K) for la in range(5) for lb in range(5) for lc in range(7) for K in (1, 3, 6)]
 
 
 # --------------------------------------------------------------------------
@@ -189,7 +189,7 @@ def cluster(shape, orb_recipe, aux_recipe, seed, spacing=1.8, jitter=0.3, exp_lo
     return Cluster(len(coords), coords, orb, aux)
 
 
-def config3(shape=(8, 8, 4)):
+def cluster256_dfj(shape=(8, 8, 4)):
     """256-atom jittered grid (1.8 bohr), orbital 4s3p2d1f (K=6/3/1/1),
     aux 10s7p5d3f2g1h (K=1)."""
     return cluster(shape, ORB_RECIPE_DFJ, AUX_RECIPE_DFJ, SEED_BASE + 2)
@@ -202,12 +202,12 @@ def density(rng, n, rank=None):
     return C @ C.T
 
 
-def config5(shape=(4, 4, 4)):
+def cluster64_grad(shape=(4, 4, 4)):
     """64-atom cluster, orbital 3s2p2d1f1g (L<=4), aux 8s6p5d4f3g2h (L<=5)."""
     return cluster(shape, ORB_RECIPE_SMALL, AUX_RECIPE_GRAD, SEED_BASE + 4)
 
 
-def config4_sizes():
+def batch16_sizes():
     """16 molecule sizes n_i = round(20 * 20^(i/15)): 20 ... 400 atoms."""
     return [int(round(20 * 20 ** (i / 15))) for i in range(16)]
 
@@ -238,11 +238,11 @@ def molecule(natom, seed, orb_recipe=None, aux_recipe=None, orb_fraction=1.0, au
     return Cluster(natom, coords, orb, aux)
 
 
-def config4(orb_fraction=0.25):
+def batch16_molecules(orb_fraction=0.25):
     """Batched uneven workload: 16 molecules of 20-400 atoms, orbital 3s2p2d1f1g
     (K=6/3/1/1/1), aux 8s6p5d4f3g2h1i (K=1), every class up to (gg|i) mixed.
     A fixed fraction of each molecule's orbital shells is kept (uniform,
     seeded; identical for the batched and the per-class runs), which scales
     the shell pairs by about its square and leaves every pair's ket list, and
     so the tile fill, as in the full molecule."""
-    return [molecule(n, SEED_BASE + 3 + 100 * i, orb_fraction=orb_fraction) for i, n in enumerate(config4_sizes())]
+    return [molecule(n, SEED_BASE + 3 + 100 * i, orb_fraction=orb_fraction) for i, n in enumerate(batch16_sizes())]

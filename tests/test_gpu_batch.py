@@ -1,4 +1,4 @@
-"""Batched uneven workload (configs[3] recipe, not in the paper): several
+"""Batched uneven workload (16 molecules of 20-400 atoms, not in the paper): several
 molecules' DF-J builds, every class mixed, as one persistent kernel inside one
 CUDA graph, checked against the per-class launches and the oracle."""
 import os

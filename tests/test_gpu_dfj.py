@@ -75,10 +75,10 @@ def test_dfj_screening_keeps_everything_at_zero_tol(lx):
     assert plan.ntasks == nsh * (nsh + 1) // 2 * cl.aux.nshell
 
 
-def test_dfj_config3_sampled(lx):
-    """256-atom cluster (configs[2] recipe): J blocks of 64 random shell pairs
+def test_dfj_256_atoms_sampled(lx):
+    """256-atom cluster (8x8x4 grid): J blocks of 64 random shell pairs
     and gamma of 3 random ket shells against the FP64 oracle."""
-    cl = W.config3()
+    cl = W.cluster256_dfj()
     D, c = inputs(cl, 3)
     plan, g, J = run_gpu(lx, cl, D, c)
     ao = oracle.ao_offsets(cl.orb)

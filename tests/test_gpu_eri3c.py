@@ -30,9 +30,9 @@ def run(lx, p, bra_pure=True):
     return out.cpu().numpy()
 
 
-def test_config1_full(lx):
+def test_ppd_64x32_full(lx):
     """(pp|d), K=1, 64 pairs x 32 aux shells: every integral."""
-    p = W.config1()
+    p = W.ppd_64x32()
     assert_parity(run(lx, p), p)
 
 

@@ -6,7 +6,7 @@ Checks, following the target's statement:
     independently) on the same screened task list, 1e-11 relative to max|F|;
   - sum of forces = 0 to 1e-10 max|F|;
   - central finite differences of the GPU energy (h = 1e-4 bohr) on the
-    64-atom configs[4] cluster, 12 random coordinates, 1e-7 relative to max|F|;
+    64-atom cluster (4x4x4 grid), 12 random coordinates, 1e-7 relative to max|F|;
   - torch.autograd through DFJEnergy returns the same gradient.
 """
 import numpy as np
@@ -60,8 +60,8 @@ def test_gradient_three_atoms_fp64_oracle(lx):
     assert np.abs(Go.sum(axis=0)).max() <= 1e-9 * np.abs(Go).max()
 
 
-def test_gradient_finite_differences_config5(lx):
-    cl = W.config5()
+def test_gradient_finite_differences_64_atoms(lx):
+    cl = W.cluster64_grad()
     D, c = dc(cl, 7)
     Dt, ct = torch.tensor(D, device="cuda"), torch.tensor(c, device="cuda")
     R0 = cl.coords.copy()

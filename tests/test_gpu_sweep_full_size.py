@@ -1,4 +1,4 @@
-"""Parity at the full configs[1] sizes, in the launch configuration bench.py
+"""Parity at the full per-class sweep sizes, in the launch configuration bench.py
 times: every one of the 525 (la, lb <= 4 | lc <= 6, K_ab in {1,3,6}) classes at
 4096 pairs x 512 ket shells (Eri3cPlan with the planner's own shapes, as the
 bench builds it), with a seeded sample of (pair, ket) blocks per class checked
@@ -33,7 +33,7 @@ def lx():
 
 
 def check_class(lx, la, lb, lc, K):
-    p = W.config2_class(la, lb, lc, K)
+    p = W.sweep_class(la, lb, lc, K)
     plan = lx.Eri3cPlan(p.orb, p.aux, p.pairs, p.auxs, bra_pure=True)
     out = plan.execute()
     rng = np.random.default_rng(1000 * (la * 100 + lb * 10 + lc) + K)
@@ -55,10 +55,10 @@ def check_class(lx, la, lb, lc, K):
     return ok.all(), 1.0 - strict.mean(), int(ok.size)
 
 
-def test_config2_all_classes_full_size_sampled(lx):
+def test_sweep_all_classes_full_size_sampled(lx):
     failures = []
     worst = 0.0
-    for (la, lb, lc, K) in W.CONFIG2_CLASSES:
+    for (la, lb, lc, K) in W.SWEEP_CLASSES:
         ok, miss, n = check_class(lx, la, lb, lc, K)
         worst = max(worst, miss)
         if not ok or miss > STRICT_MISS_FRACTION:
