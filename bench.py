@@ -126,17 +126,33 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
+def rank_problem(la, lb, lc, K, npair, naux, rank, product_k=False):
+    """The class problem rank `rank` evaluates: rank 0 the sweep recipe itself,
+    every other rank the same recipe with its own seed (weak scaling: each
+    rank a sweep of its own synthetic shells, no data exchanged)."""
+    from paper_2210_03192_gb300 import workloads as W
+    if rank == 0:
+        return W.sweep_class(la, lb, lc, K, npair, naux, product_reading=product_k)
+    return W.class_problem(la, lb, lc, npair, naux, *((K, 1) if product_k else (K, K)), 1,
+                           box=20.0, exp_lo=0.05, exp_hi=1.0e4,
+                           seed=W.SEED_BASE + 7919 * rank + la * 100 + lb * 10 + lc + 1000 * K)
+
+
+def max_over_ranks(value, dist, device):
+    """The largest `value` over all ranks (the step time of the slowest rank)."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def build_plans(classes, args, rank):
     import paper_2210_03192_gb300 as lx
-    from paper_2210_03192_gb300 import workloads as W
     plans = []
     for (la, lb, lc, K) in classes:
-        p = W.sweep_class(la, lb, lc, K, args.npair, args.naux, product_reading=args.product_k)
-        if rank:
-            # weak scaling: every rank evaluates a sweep of its own synthetic shells
-            p = W.class_problem(la, lb, lc, args.npair, args.naux, *((K, 1) if args.product_k else (K, K)), 1,
-                                box=20.0, exp_lo=0.05, exp_hi=1.0e4, seed=W.SEED_BASE + 7919 * rank + la * 100 +
-                                lb * 10 + lc + 1000 * K)
+        p = rank_problem(la, lb, lc, K, args.npair, args.naux, rank, args.product_k)
         plan = lx.Eri3cPlan(p.orb, p.aux, p.pairs, p.auxs, bra_pure=True)
         Kab = K * K if not args.product_k else K
         flops = lx.class_flops(la, lb, lc, Kab, 1, True) * plan.npair * plan.naux
@@ -193,11 +209,7 @@ def run_ours(args, rank, world, dist):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
     total_int = sum(p["nint"] for p in plans) * args.steps * world
     total_flops = sum(p["flops"] for p in plans) * args.steps
     # per-class table and dominant class
