@@ -155,3 +155,28 @@ def test_shape_query_budgets_and_hints(tmp_path):
         lx.shape_hint(4, 4, 1, 36, 1, 4)
     with pytest.raises(lx.LibraryError):
         lx.shape_query(9, 4, 1, 36, 1, 512, 2)
+
+
+def test_committed_shape_hints_file():
+    """The shipped GB300 hints: every line a valid class with a 1-3 CTA target,
+    loadable, and each hinted shape fits the shared memory of its target."""
+    import paper_2210_03192_gb300 as lx
+    lines = []
+    with open(lx.HINTS_GB300) as f:
+        for line in f:
+            fields = line.split("#", 1)[0].split()
+            if fields:
+                lines.append(tuple(int(x) for x in fields))
+    assert lines
+    for (la, lb, lc, pure, kab, kc, ctas) in lines:
+        assert 0 <= la <= 4 and 0 <= lb <= 4 and 0 <= lc <= 6 and pure == 1 and kab in (1, 9, 36) and kc == 1
+        assert ctas in (1, 3)
+    try:
+        assert lx.load_shape_hints() == len(lines)
+        for (la, lb, lc, pure, kab, kc, ctas) in lines:
+            T, G, mode, sb = lx.shape_query(la, lb, lc, kab, kc, 512, 0)
+            assert (T, G, mode, sb) == lx.shape_query(la, lb, lc, kab, kc, 512, ctas)
+            assert sb <= 233472 // ctas - 1024 or ctas == 1
+    finally:
+        for (la, lb, lc, pure, kab, kc, ctas) in lines:
+            lx.shape_hint(la, lb, lc, kab, kc, 0)
