@@ -463,10 +463,13 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
           ClassDesc& d = L.desc;
           if (fill_class_desc(d, *ct, *dc, ds, o, dk[o], Kab, g.Kc, fill_bound(dsub[o], g.counts, cmax)) < 0)
             return dfail(LX3C_ENOTSUP, "derivative class does not fit in shared memory");
-          const int nch = std::max(1, (nmax + 31) / 32);
+          // entries per partial sum: balances the partial's FMA chain (E (nC+1))
+          // against the final sum over the nmax / E partials of an axis
+          const int E = std::max(1, std::min(32, (int)std::lround(std::sqrt((double)nmax / (d.nC + 1)))));
+          const int nch = std::max(1, (nmax + E - 1) / E);
           const int nAp = 2 * g.la + 1, ncA = ncart(g.la), nBp = 2 * g.lb + 1, ncB = ncart(g.lb);
-          d.g_base = d.smem_doubles;
-          d.smem_doubles += nAp * ncB + ncA * ncB + d.T * 3 * nch;
+          d.g_echunk = E;
+          d.g_base = place_epilogue_scratch(d, nAp * ncB + ncA * ncB + (long long)d.T * 3 * nch);
           if (d.smem_doubles * 8 > 232448) return dfail(LX3C_ENOTSUP, "gradient epilogue does not fit");
           d.g_centre = centre;
           d.g_nAp = nAp; d.g_ncA = ncA; d.g_nBp = nBp; d.g_ncB = ncB; d.g_nch = nch;
@@ -653,10 +656,8 @@ bool retile(DfjLaunch& L, const DfjGroup& g, const DevState* ds, int T) {
   sh.mode = mode;
   ClassDesc nd = d;
   fill_layout(nd, ct, sh);
-  int extra = d.digest == 2 ? (d.g_nAp * d.g_ncB + d.g_ncA * d.g_ncB) : 0;
   if (d.digest == 2) {
-    nd.g_base = nd.smem_doubles;
-    nd.smem_doubles += extra + T * 3 * d.g_nch;
+    nd.g_base = place_epilogue_scratch(nd, d.g_nAp * d.g_ncB + d.g_ncA * d.g_ncB + (long long)T * 3 * d.g_nch);
   } else if (d.digest == 1) {
     set_digest_scratch(nd);
   }

@@ -650,7 +650,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       const int dnA = d.onA, dnB = d.onB;  // derivative class bra dims, caller order
       for (int w = tid; w < tv * 3 * nch; w += kThreads) {
         const int t = w / (3 * nch), rem = w - t * 3 * nch, ax = rem / nch, k = rem - ax * nch;
-        const int e0 = d.gstart[ax] + k * 32, e1 = min(d.gstart[ax + 1], e0 + 32);
+        const int e0 = d.gstart[ax] + k * d.g_echunk, e1 = min(d.gstart[ax + 1], e0 + d.g_echunk);
         const double* cv = d.cvec + __ldg(d.aux_ao + aux0 + t);
         double s = 0.0;
         for (int e = e0; e < e1; ++e) {
@@ -668,8 +668,14 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       const int tatom = d.g_centre ? pat.y : pat.x;
       for (int w = tid; w < tv * 3; w += kThreads) {
         const int t = w / 3, ax = w - t * 3;
-        double s = 0.0;
-        for (int k = 0; k < nch; ++k) s += part[(t * 3 + ax) * nch + k];
+        double s0 = 0.0, s1 = 0.0;
+        int k = 0;
+        for (; k + 1 < nch; k += 2) {
+          s0 += part[(t * 3 + ax) * nch + k];
+          s1 += part[(t * 3 + ax) * nch + k + 1];
+        }
+        if (k < nch) s0 += part[(t * 3 + ax) * nch + k];
+        const double s = s0 + s1;
         atomicAdd(d.grad + 3 * tatom + ax, s);
         atomicAdd(d.grad + 3 * __ldg(d.aux_atom + aux0 + t) + ax, -s);
       }

@@ -122,6 +122,7 @@ struct ClassDesc {
   // entries are grouped by axis (gstart[0..3]).
   int g_centre;            // 0: derivative on the pair's first shell, 1: second
   int g_nAp, g_ncA, g_nBp, g_ncB, g_nch, g_base;
+  int g_echunk;            // map entries per partial sum (g_nch partials per axis)
   int gstart[4];
   const int4* gmap;
   const double* Ta;        // [2la+1][ncart(la)] of the original la
@@ -223,6 +224,10 @@ struct LaunchShape {
 // stage region the final block does not occupy, or appends it when that region
 // is too small; updates d.dscr and d.smem_doubles.
 void set_digest_scratch(ClassDesc& d);
+// Base (doubles) of `need` doubles of epilogue scratch: the stage region the
+// final block does not occupy when it is large enough, else appended (grows
+// d.smem_doubles).
+int place_epilogue_scratch(ClassDesc& d, long long need);
 LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit);
 LaunchShape choose_shape_for(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit, int ctas);
 void set_shape_hint(int la, int lb, int lc, int bra_pure, int Kab, int Kc, int ctas);

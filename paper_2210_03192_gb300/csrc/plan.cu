@@ -554,17 +554,18 @@ LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux,
   return choose_shape_for(ct, Kab, Kc, naux, smem_limit, h > 0 ? h : 2);
 }
 
-void set_digest_scratch(ClassDesc& d) {
-  const long long need = (long long)d.onA * d.onB + (long long)d.T * d.nC;
+int place_epilogue_scratch(ClassDesc& d, long long need) {
   const bool out_in_x = d.OUT.base == d.V.base;
   const long long free_base = out_in_x ? d.P.base : d.V.base;
   const long long free_size = out_in_x ? (long long)d.V.base - d.P.base : (long long)d.smem_doubles - d.V.base;
-  if (need <= free_size) {
-    d.dscr = (int)free_base;
-  } else {
-    d.dscr = d.smem_doubles;
-    d.smem_doubles += (int)need;
-  }
+  if (need <= free_size) return (int)free_base;
+  const int base = d.smem_doubles;
+  d.smem_doubles += (int)need;
+  return base;
+}
+
+void set_digest_scratch(ClassDesc& d) {
+  d.dscr = place_epilogue_scratch(d, (long long)d.onA * d.onB + (long long)d.T * d.nC);
 }
 
 void fill_layout(ClassDesc& d, const ClassTables& ct, const LaunchShape& sh) {
