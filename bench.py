@@ -294,6 +294,17 @@ def oracle_sample(classes, args, seconds):
                        "%.1f s" % (npr, len(probs), ints, dt), seconds=dt, ints=ints)
 
 
+def sweep_config(args, classes, world):
+    """The workload both arms report on (the reference arm times a bounded
+    sample of it, stated in its cpu_baseline)."""
+    nint = sum(args.npair * args.naux * (2 * la + 1) * (2 * lb + 1) * (2 * lc + 1) for (la, lb, lc, _) in classes)
+    return dict(workload="per-class sweep: every (la,lb<=4|lc<=6) class, K_ab in {1,3,6} (K_a=K_b=K_ab, K_c=1), "
+                         "%d pairs x %d aux shells per class, all-pure, blocks written to HBM" % (args.npair, args.naux),
+                classes=len(classes), integrals_per_step=nint,
+                l2="each step writes the whole sweep's blocks (TB-scale, far above the 129 MB L2); no flush",
+                parallelism="dp%d (independent sweeps per rank)" % world)
+
+
 def run_reference(args, rank, world):
     classes = class_list(args)
     res = []
@@ -306,8 +317,7 @@ def run_reference(args, rank, world):
                 steps=args.steps, warmup=args.warmup, ms_per_step=round(1000 * res[-1]["seconds"], 2),
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic (per-class sweep recipe, seeded)", impl="reference",
-                config=dict(workload="per-class sweep (la,lb<=4|lc<=6), K_ab in {1,3,6}, all-pure; oracle sample",
-                            classes=len(classes)),
+                config=sweep_config(args, classes, world),
                 cpu_baseline=dict(value=v, unit="Gints/s", cores=res[-1]["cores"], kind="oracle",
                                   sample=res[-1]["sample"]),
                 e2e=dict(value=v, unit="Gints/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -342,12 +352,7 @@ def main():
         steps=args.steps, warmup=args.warmup, ms_per_step=round(res["ms"] / args.steps, 2),
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
         data="synthetic (per-class sweep recipe, seeded; no public dataset)",
-        config=dict(workload="per-class sweep: every (la,lb<=4|lc<=6) class, K_ab in {1,3,6} (K_a=K_b=K_ab, K_c=1), "
-                             "%d pairs x %d aux shells per class, all-pure, blocks written to HBM" % (args.npair,
-                                                                                                   args.naux),
-                    classes=len(classes), integrals_per_step=res["total_int"] // (args.steps * world),
-                    l2="each step writes the whole sweep's blocks (TB-scale, far above the 129 MB L2); no flush",
-                    parallelism="dp%d (independent sweeps per rank)" % world,
+        config=dict(sweep_config(args, classes, world),
                     tile_shapes=("planner default + %d tuned hints (shape_hints_gb300.txt)" % getattr(args, "hints", 0)
                                  if getattr(args, "hints", 0) else "planner default")),
         roofline=res["roofline"], cpu_baseline=cpu, clocks=res["clocks"], gpu_launches=res["launches"],
