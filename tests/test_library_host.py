@@ -180,3 +180,36 @@ def test_committed_shape_hints_file():
     finally:
         for (la, lb, lc, pure, kab, kc, ctas) in lines:
             lx.shape_hint(la, lb, lc, kab, kc, 0)
+
+
+def test_more_entry_points_reject_bad_arguments_on_host():
+    """Argument checks that run before any device work: null or empty inputs,
+    out-of-range sizes and modes give LX3C_EINVAL (-1) or LX3C_ENOTSUP (-2)
+    with an error message, on every family of calls."""
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    # DF-J / gradient
+    assert L.lx3c_dfj_plan(ctypes.byref(h), None, None, 1e-12, 0, None) == -1
+    assert L.lx3c_dfj_execute(None, None, None, None, None, None) == -1
+    assert L.lx3c_dfj_energy(None, None, None, None, None, None) == -1
+    assert L.lx3c_dfj_grad(None, None, None, None, None) == -1
+    assert L.lx3c_dfj_info(None, None, 0) == -1
+    assert L.lx3c_dfj_group(None, 0, None, None, None, None) == -1
+    # batch
+    assert L.lx3c_batch_plan(ctypes.byref(h), 0, None, None, 1e-12, None, None) == -1
+    assert L.lx3c_batch_bind(None, None, None, None, None, None) == -1
+    assert L.lx3c_batch_execute(None, 1, None) == -1
+    assert L.lx3c_batch_info(None, None, 0) == -1
+    # allocation-free class call: limits checked before the device is touched
+    nul = [None] * 9
+    assert L.lx3c_eri3c_noalloc(7, 0, 0, 1, 1, 1, 1, *nul, 1, None, 1, None, None) == -2   # l beyond 6
+    assert L.lx3c_eri3c_noalloc(1, 0, 0, 17, 1, 1, 1, *nul, 1, None, 1, None, None) == -2  # K beyond 16
+    assert L.lx3c_eri3c_noalloc(1, 0, 0, 1, 1, 1, 1, *nul, 0, None, 1, None, None) == -1   # empty pair list
+    assert L.lx3c_eri3c_noalloc(1, 0, 0, 1, 1, 1, 1, *nul, 1, None, 1, None, None) == -1   # null pointers
+    msg = L.lx3c_last_error()
+    assert msg and b"null" in msg
+    # host-buffer path and Boys
+    assert L.lx3c_eri3c_host(0, None, None, None, None, None, 0, None, None, None, None, None, None, 0, None, 0,
+                             1, None, None) == -1
+    assert L.lx3c_boys(None, 4, 3, None, None) == -1
+    assert L.lx3c_boys(None, 1, 25, None, None) == -1
