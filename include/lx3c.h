@@ -167,6 +167,18 @@ lx3c_status lx3c_class_flops(int la, int lb, int lc, int Kab, int Kc, int bra_pu
  * Both return LX3C_EINVAL for arguments out of range.
  */
 lx3c_status lx3c_shape_hint(int la, int lb, int lc, int bra_pure, int kab, int kc, int ctas_per_sm);
+
+/*
+ * Self-check of the planner's host tables for class (la, lb | lc) (not in the
+ * paper): every VRR1 (Eq. vrr1) item reads only entries formed at lower
+ * levels and every entry above level 0 is formed exactly once; weight,
+ * accumulator, gather (Sec. 2.5.4), ket/bra transform and HRR (Eq. hrr)
+ * indices are in range; HRR level j reads only level j-1; the gather order is
+ * a permutation by descending term count and its sliced-ELL copy holds the
+ * CSR terms, padded with zero-coefficient terms.  Host only.  Returns LX3C_OK,
+ * or LX3C_EINVAL naming the first violation (lx3c_last_error).
+ */
+lx3c_status lx3c_class_tables_check(int la, int lb, int lc, int bra_pure);
 lx3c_status lx3c_shape_query(int la, int lb, int lc, int bra_pure, int kab, int kc, int64_t naux, int ctas_per_sm,
                              int32_t* out);
 

@@ -59,6 +59,7 @@ EXPORTS = {
     "lx3c_cvrr2_expansion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "lx3c_shape_hint": (ctypes.c_int, [ctypes.c_int] * 7),
+    "lx3c_class_tables_check": (ctypes.c_int, [ctypes.c_int] * 4),
     "lx3c_shape_query": (ctypes.c_int, [ctypes.c_int] * 6 + [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
 }
 

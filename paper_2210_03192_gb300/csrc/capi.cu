@@ -610,6 +610,18 @@ lx3c_status lx3c_boys(const double* T, int64_t n, int mmax, double* out, void* s
   return LX3C_OK;
 }
 
+lx3c_status lx3c_class_tables_check(int la, int lb, int lc, int bra_pure) {
+  if (la < 0 || lb < 0 || lc < 0 || la > LX3C_LMAX_ORB + 1 || lb > LX3C_LMAX_ORB + 1 || lc > LX3C_LMAX_AUX)
+    return fail(LX3C_EINVAL, "class_tables_check: bad argument");
+  try {
+    const std::string msg = check_class_tables(class_tables(la, lb, lc, bra_pure ? 1 : 0));
+    if (!msg.empty()) return fail(LX3C_EINVAL, "class tables: " + msg);
+  } catch (std::exception& e) {
+    return fail(LX3C_ENOTSUP, e.what());
+  }
+  return LX3C_OK;
+}
+
 lx3c_status lx3c_shape_hint(int la, int lb, int lc, int bra_pure, int kab, int kc, int ctas_per_sm) {
   if (la < 0 || lb < 0 || lc < 0 || la > LX3C_LMAX_ORB + 1 || lb > LX3C_LMAX_ORB + 1 || lc > LX3C_LMAX_AUX ||
       kab < 1 || kc < 1 || ctas_per_sm < 0 || ctas_per_sm > 3)

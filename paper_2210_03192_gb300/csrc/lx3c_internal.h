@@ -228,6 +228,7 @@ void set_digest_scratch(ClassDesc& d);
 // final block does not occupy when it is large enough, else appended (grows
 // d.smem_doubles).
 int place_epilogue_scratch(ClassDesc& d, long long need);
+std::string check_class_tables(const ClassTables& ct);  // "" when every table invariant holds
 LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit);
 LaunchShape choose_shape_for(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit, int ctas);
 void set_shape_hint(int la, int lb, int lc, int bra_pure, int Kab, int Kc, int ctas);

@@ -16,11 +16,13 @@
 #include <vector_types.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <map>
 #include <mutex>
 #include <set>
 #include <stdexcept>
+#include <string>
 #include <tuple>
 
 #include "lx3c_internal.h"
@@ -416,6 +418,97 @@ const ClassTables& class_tables(int la, int lb, int lc, int bra_pure) {
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   return cache.emplace(key, build(la, lb, lc, bra_pure ? 1 : 0)).first->second;
+}
+
+// Invariants of a class's host tables; empty string when they all hold.
+std::string check_class_tables(const ClassTables& ct) {
+  char buf[160];
+  auto bad = [&](const char* what, long long i) {
+    std::snprintf(buf, sizeof(buf), "%s (entry %lld)", what, i);
+    return std::string(buf);
+  };
+  const int Lab = ct.la + ct.lb;
+  const unsigned NV = (unsigned)ct.NV, NW = (unsigned)ct.NW, NF = (unsigned)ct.NF, NACC = (unsigned)ct.NACC;
+  if ((int)ct.vlev_start.size() != Lab + 1) return "VRR1 level table size";
+  // VRR1: indices in range; every entry above level 0 written once; level e
+  // reads only entries written before it (levels are contiguous and ordered)
+  std::vector<int> written(NV, 0);
+  for (int e = 1; e <= Lab; ++e) {
+    unsigned lo = NV;
+    for (int i = ct.vlev_start[e - 1]; i < ct.vlev_start[e]; ++i) lo = std::min(lo, ct.vtab[i].x & 0xFFFF);
+    for (int i = ct.vlev_start[e - 1]; i < ct.vlev_start[e]; ++i) {
+      const uint4 it = ct.vtab[i];
+      const unsigned dst = it.x & 0xFFFF, a = it.x >> 16, an = it.y & 0xFFFF, b = it.y >> 16, bn = it.z & 0xFFFF;
+      const unsigned axis = (it.z >> 16) & 0xF, nq = (it.z >> 20) & 0xF;
+      if (dst >= NV || a >= lo || an >= lo || axis > 2 || (nq && (b >= lo || bn >= lo)))
+        return bad("VRR1 item index out of range or not yet formed", i);
+      ++written[dst];
+    }
+  }
+  for (unsigned v = 0; v < NV; ++v)
+    if (written[v] != (v <= (unsigned)Lab ? 0 : 1)) return bad("VRR1 entry not formed exactly once", v);
+  // weights and accumulators
+  for (size_t i = 0; i < ct.wtab.size(); ++i) {
+    const int4 w = ct.wtab[i];
+    const unsigned cnt = (unsigned)w.z >> 16;
+    const unsigned src[4] = {(unsigned)w.x >> 16, (unsigned)w.y & 0xFFFF, (unsigned)w.y >> 16, (unsigned)w.z & 0xFFFF};
+    if (((unsigned)w.x & 0xFFFF) >= NW || cnt > 4) return bad("weight item", (long long)i);
+    for (unsigned k = 0; k < cnt; ++k)
+      if (src[k] >= NF) return bad("weight factor index", (long long)i);
+  }
+  if (ct.atab.size() != NACC) return "accumulator table size";
+  for (size_t i = 0; i < ct.atab.size(); ++i)
+    if ((ct.atab[i] & 0xFFFF) >= NV || (ct.atab[i] >> 16) >= NW) return bad("accumulator index", (long long)i);
+  // gather: CSR and its sliced-ELL copy hold the same terms
+  const int ngt = ct.nkrow * ct.ncc;
+  if ((int)ct.gptr.size() != ngt + 1 || (int)ct.gdst.size() != ngt) return "gather table size";
+  std::vector<int> seen(ngt, 0);
+  for (int r = 0; r < ngt; ++r) {
+    if (ct.gdst[r] < 0 || ct.gdst[r] >= ngt || seen[ct.gdst[r]]++) return bad("gather order not a permutation", r);
+    if (r && ct.gptr[ct.gdst[r] + 1] - ct.gptr[ct.gdst[r]] > ct.gptr[ct.gdst[r - 1] + 1] - ct.gptr[ct.gdst[r - 1]])
+      return bad("gather order not by descending term count", r);
+  }
+  for (int id = 0; id < ngt; ++id)
+    if (ct.gptr[id + 1] < ct.gptr[id]) return bad("gather row pointers", id);
+  for (size_t q = 0; q < ct.gterm.size(); ++q)
+    if ((ct.gterm[q] & 0xFFFFF) >= NACC || (ct.gterm[q] >> 20) >= ct.pal.size()) return bad("gather term", (long long)q);
+  if ((int)ct.gslice.size() != (ngt + 31) / 32) return "sliced ELL slice count";
+  for (int sl = 0; sl < (int)ct.gslice.size(); ++sl)
+    for (int l = 0; l < 32; ++l) {
+      const int r = 32 * sl + l;
+      const int id = r < ngt ? ct.gdst[r] : -1;
+      const int cnt = id >= 0 ? ct.gptr[id + 1] - ct.gptr[id] : 0;
+      if (cnt > ct.gslice[sl].y) return bad("sliced ELL row longer than its slice", r);
+      for (int j = 0; j < ct.gslice[sl].y; ++j) {
+        const size_t q = (size_t)ct.gslice[sl].x + 32 * j + l;
+        if (q >= ct.gell.size()) return bad("sliced ELL entry out of range", r);
+        const unsigned e = ct.gell[q];
+        if (j < cnt ? e != ct.gterm[ct.gptr[id] + j]
+                    : ((e >> 20) >= ct.pal.size() || ct.pal[e >> 20] != 0.0 || (e & 0xFFFFF) >= NACC))
+          return bad("sliced ELL differs from the CSR terms", r);
+      }
+    }
+  // ket transform
+  if ((int)ct.kptr.size() != ct.nC + 1) return "ket table size";
+  for (size_t q = 0; q < ct.kent.size(); ++q)
+    if (ct.kent[q].x < 0 || ct.kent[q].x >= ct.ncc || ct.kent[q].y < 0 || ct.kent[q].y >= (int)ct.pal.size())
+      return bad("ket entry", (long long)q);
+  // HRR: level j rows built from rows of level j-1
+  for (int j = 1; j <= ct.lb; ++j)
+    for (int i = ct.hstart[j]; i < ct.hstart[j + 1]; ++i) {
+      const int4 h = ct.htab[i];
+      if (h.x < 0 || h.x >= ct.hrows[j] || h.y < 0 || h.y >= ct.hrows[j - 1] || h.z < 0 || h.z >= ct.hrows[j - 1] ||
+          h.w < 0 || h.w > 2)
+        return bad("HRR row", i);
+    }
+  // bra transforms
+  if (ct.nbA)
+    for (size_t q = 0; q < ct.baent.size(); ++q)
+      if (ct.baent[q].x < 0 || ct.baent[q].x >= ct.ncA) return bad("bra A entry", (long long)q);
+  if (ct.nbB)
+    for (size_t q = 0; q < ct.bbent.size(); ++q)
+      if (ct.bbent[q].x < 0 || ct.bbent[q].x >= ct.ncB) return bad("bra B entry", (long long)q);
+  return "";
 }
 
 // ---------------------------------------------------------------------------

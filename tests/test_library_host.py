@@ -213,3 +213,18 @@ def test_more_entry_points_reject_bad_arguments_on_host():
                              1, None, None) == -1
     assert L.lx3c_boys(None, 4, 3, None, None) == -1
     assert L.lx3c_boys(None, 1, 25, None, None) == -1
+
+
+def test_class_tables_invariants_every_class():
+    """The planner's host tables satisfy their invariants (lx3c_class_tables_check)
+    for every integral class (pure bra, la, lb <= 4) and every derivative class
+    the gradient uses (Cartesian bra, one shell raised to l <= 5), lc <= 6."""
+    L = _lib.load()
+    cases = [(la, lb, lc, 1) for la in range(5) for lb in range(5) for lc in range(7)]
+    cases += [(la, lb, lc, 0) for la in range(6) for lb in range(6) if la + lb <= 9 for lc in range(7)]
+    bad = []
+    for (la, lb, lc, pure) in cases:
+        if L.lx3c_class_tables_check(la, lb, lc, pure) != 0:
+            bad.append((la, lb, lc, pure, L.lx3c_last_error()))
+    assert not bad, bad[:5]
+    assert L.lx3c_class_tables_check(-1, 0, 0, 1) == -1
