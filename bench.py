@@ -12,7 +12,12 @@ max-over-ranks device time of the K timed steps (Gints/s).  Per-class
 throughput and the FP64 roofline fraction of the dominant class are included.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--classes la,lb,lc,K ...] [--quick]
+                  [--classes la,lb,lc,K ...] [--no-e2e] [--no-cpu] [--no-hints]
+
+The end-to-end leg (e2e) repeats the sweep through the host-buffer call
+lx3c_eri3c_host (host shell tables in, page-locked host blocks out).  The
+cpu_baseline leg and --impl reference time the CPU oracle on a bounded sample
+of the same workload.
 """
 import argparse
 import json
@@ -65,10 +70,6 @@ def class_list(args):
     if args.classes:
         return [tuple(int(x) for x in c.split(",")) for c in args.classes]
     return list(W.SWEEP_CLASSES)
-
-
-def nint(la, lb, lc):
-    return (2 * la + 1) * (2 * lb + 1) * (2 * lc + 1)
 
 
 # ---------------------------------------------------------------------------
