@@ -208,7 +208,9 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  *   Q_ab = sum over primitive pairs of |c_a c_b| exp(-za zb/g AB^2)
  *   sqrt(2 pi^{5/2}/(g^2 sqrt(2g))) (|PA|^2+1/(2g))^{la/2} (|PB|^2+1/(2g))^{lb/2}
  *   and Q_P = sum |c_c| sqrt(2 pi^{5/2}/(z^2 sqrt(2z))) (1/(2z))^{lc/2}, an
- *   estimate of sqrt(max|(ab|ab)|) and sqrt(max|(P|P)|).  Pass 0 to keep all.
+ *   estimate of sqrt(max|(ab|ab)|) and sqrt(max|(P|P)|) -- an estimate, not a
+ *   strict bound: dropped triples can hold integrals up to ~10x the tolerance.
+ *   Pass 0 to keep all.
  *   Returns LX3C_ENOTSUP for orbital shells above LX3C_LMAX_ORB.
  * lx3c_dfj_execute: D (device, nao x nao row-major, symmetric), c (device,
  *   naux_ao) in; gamma (device, naux_ao) and J (device, nao x nao, symmetric)
