@@ -8,11 +8,20 @@ blocks written to HBM.  Synthetic shells: centres uniform in a 20-bohr cube,
 exponents log-uniform in [0.05, 1e4], coefficients uniform in [0.1, 1].
 
 Output: one JSON line (rank 0).  value = integrals computed by all ranks /
-max-over-ranks device time of the K timed steps (Gints/s).  Per-class
-throughput and the FP64 roofline fraction of the dominant class are included.
+max-over-ranks device time of the K timed steps (Gints/s).  The line carries
+the FP64 roofline of the dominant class, a short list of the slowest classes
+(the full per-class table goes to --per-class-out), and one-off measurements
+taken after the timed sweep, each with its own clock record:
+  config1  (pp|d), 64 pairs x 32 ket shells: ms per evaluation
+  dfj      256-atom DF-J build: fused gamma+J, gamma-only, J-only seconds
+  batch    16 molecules in one graph launch vs per-class launches
+  grad     64-atom DF-J energy forward, gradient backward, fwd+bwd
+  fp64_peak_measured  live FP64 FMA rate (lx3c_fp64_rate)
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--classes la,lb,lc,K ...] [--no-e2e] [--no-cpu] [--no-hints]
+                  [--classes la,lb,lc,K ...] [--npair N] [--naux N]
+                  [--extras config1,dfj,batch,grad | --extras none]
+                  [--no-e2e] [--no-cpu] [--no-hints] [--per-class-out FILE]
 
 The end-to-end leg (e2e) repeats the sweep through the host-buffer call
 lx3c_eri3c_host (host shell tables in, page-locked host blocks out).  The
@@ -34,10 +43,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # FP64 roofline denominator: GB300 has 152 SMs issuing 2 DFMA per clock each
-# (4 flops/clk/SM) at up to 2070 MHz; the measured DFMA microbenchmark on this
-# pool gave 1191.9 GFLOP/s at the clocks it ran at.
+# (4 flops/clk/SM) at up to 2070 MHz, 1258.6 GFLOP/s (the nominal 1.25 TFLOP/s
+# FP64 figure).  The bench also measures the FMA rate live (lx3c_fp64_rate)
+# and reports it beside this figure.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
-FP64_PEAK_MEASURED = 1191.9
 
 # DRAM traffic of the (gg|i) K_ab=6 class per pair (512 ket shells, both oriented
 # launches), from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
@@ -62,6 +71,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--per-class-out", default=None, help="write the per-class table to this JSON file")
+    ap.add_argument("--extras", default="config1,dfj,batch,grad",
+                    help="one-off measurements after the timed sweep (comma list, or 'none')")
     return ap.parse_args()
 
 
@@ -224,22 +235,27 @@ def run_ours(args, rank, world, dist):
     dms = per_class[dom][0] / max(per_class[dom][1], 1)
     ach = plans[dom]["flops"] / dms / 1e6
     l3 = [r["frac"] for r in table if sum(r["cls"][:3]) >= 3]
+    traffic = None
+    if plans[dom]["cls"] == (4, 4, 6, 6) and args.naux == 512 and not args.product_k:
+        traffic = round(GGI_K6_DRAM_BYTES_PER_PAIR * args.npair)
     res = dict(ms=ms, total_int=total_int, total_flops=total_flops, table=table, clocks=clk, setup_s=setup_s,
                launches=launches_per_step * args.steps,
                roofline=dict(bound="alu", achieved=round(ach, 2), peak=round(FP64_PEAK_GFLOPS, 1), unit="GFLOP/s",
-                             frac=round(ach / FP64_PEAK_GFLOPS, 4),
-                             traffic=(round(GGI_K6_DRAM_BYTES_PER_PAIR * args.npair)
-                                      if plans[dom]["cls"] == (4, 4, 6, 6) and args.naux == 512 and not args.product_k
-                                      else None),
-                             traffic_source="ncu dram bytes, both launches, 64 pairs x 512 kets, scaled by pairs",
-                             kernel="eri3c_kernel class (%d%d|%d) K_ab=%d" % plans[dom]["cls"],
-                             peak_source="152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit counts); "
-                                         "measured DFMA microbenchmark %.1f" % FP64_PEAK_MEASURED,
+                             frac=round(ach / FP64_PEAK_GFLOPS, 4), traffic=traffic,
+                             kernel="eri3c_kernel, class (%d%d|%d) K_ab=%d" % plans[dom]["cls"],
+                             peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)",
                              flops_per_launch=plans[dom]["flops"], launch_ms=round(dms, 3)),
-               l3_frac=dict(min=min(l3) if l3 else None, median=statistics.median(l3) if l3 else None))
+               l3_frac=dict(classes=len(l3), min=min(l3) if l3 else None,
+                            median=statistics.median(l3) if l3 else None,
+                            at_least_half=sum(1 for x in l3 if x >= 0.5)))
     # e2e through the host-buffer C-ABI call
     if not args.no_e2e and rank == 0:
         res["e2e"] = run_e2e(plans, args)
+    del out
+    for p in plans:
+        p["plan"] = None
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     return res
 
 
@@ -265,6 +281,162 @@ def run_e2e(plans, args):
     tot = sum(p["nint"] for p in plans)
     return dict(value=round(tot / dt / 1e9, 4), unit="Gints/s", h2d_bytes_per_step=int(h2d),
                 d2h_bytes_per_step=int(d2h), seconds=round(dt, 3))
+
+
+# ---------------------------------------------------------------------------
+# one-off measurements after the timed sweep (configs 1, 3, 4, 5)
+# ---------------------------------------------------------------------------
+
+def event_ms(fn, reps=1):
+    """CUDA-event durations (ms) of `reps` calls of fn() on the current stream."""
+    import torch
+    st = torch.cuda.current_stream()
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def with_clocks(dev, fn):
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    try:
+        res = fn()
+    finally:
+        clk = clocks.stop()
+    res["clocks"] = clk
+    return res
+
+
+def extra_config1(dev):
+    """(pp|d), K=1, 64 pairs x 32 ket shells: the whole 92,160-integral output."""
+    import torch
+    import paper_2210_03192_gb300 as lx
+    from paper_2210_03192_gb300 import workloads as W
+    p = W.ppd_64x32()
+    plan = lx.Eri3cPlan(p.orb, p.aux, p.pairs, p.auxs, bra_pure=True)
+    out = torch.empty(plan.shape, dtype=torch.float64, device=dev)
+    for _ in range(5):
+        plan.execute(out)
+    ms = statistics.median(event_ms(lambda: plan.execute(out), 50))
+    fl = lx.class_flops(1, 1, 2, 1, 1, True) * plan.npair * plan.naux
+    return dict(workload="(pp|d) K=1, 64 pairs x 32 ket shells, all-pure", integrals=int(plan.total),
+                ms=round(ms, 4), gints_s=round(plan.total / ms / 1e6, 4),
+                frac=round(fl / ms / 1e6 / FP64_PEAK_GFLOPS, 4), launches=plan.launches, reps=50)
+
+
+def extra_dfj(dev):
+    """256-atom DF-J build: fused gamma+J, gamma-only and J-only."""
+    import torch
+    import paper_2210_03192_gb300 as lx
+    from paper_2210_03192_gb300 import workloads as W
+    cl = W.cluster256_dfj()
+    rng = np.random.default_rng(W.SEED_BASE + 2)
+    t0 = time.time()
+    plan = lx.DFJPlan(cl.orb, cl.aux, 1e-12)
+    setup = time.time() - t0
+    D = torch.tensor(W.density(rng, plan.nao), device=dev)
+    c = torch.tensor(rng.standard_normal(plan.naux_ao), device=dev)
+    gamma = torch.empty(plan.naux_ao, dtype=torch.float64, device=dev)
+    J = torch.empty((plan.nao, plan.nao), dtype=torch.float64, device=dev)
+    first = event_ms(lambda: plan.execute(D, c, gamma, J))[0]
+    fused = event_ms(lambda: plan.execute(D, c, gamma, J))[0]
+    gonly = event_ms(lambda: plan.execute(D, c, gamma, None, outputs="gamma"))[0]
+    jonly = event_ms(lambda: plan.execute(D, c, None, J, outputs="J"))[0]
+    return dict(workload="DF-J, 256-atom jittered 1.8-bohr grid, orbital 4s3p2d1f (K=6/3/1/1), aux 10s7p5d3f2g1h "
+                         "(K=1), Schwarz-type estimate at 1e-12", nao=plan.nao, naux_ao=plan.naux_ao,
+                screened_triples=plan.ntasks, integrals=plan.nint, tile_fill=round(plan.tile_fill, 4),
+                setup_s=round(setup, 2), first_build_s=round(first / 1e3, 3), fused_s=round(fused / 1e3, 3),
+                gamma_only_s=round(gonly / 1e3, 3), J_only_s=round(jonly / 1e3, 3),
+                fused_frac=round(plan.flops / fused / 1e6 / FP64_PEAK_GFLOPS, 4), launches=plan.launches)
+
+
+def extra_batch(dev):
+    """16 molecules (20-400 atoms), every class mixed: one graph launch vs per-class launches."""
+    import torch
+    import paper_2210_03192_gb300 as lx
+    from paper_2210_03192_gb300 import workloads as W
+    import oracle
+    mols = W.batch16_molecules()
+    rng = np.random.default_rng(W.SEED_BASE + 3)
+    t0 = time.time()
+    b = lx.Batch([(m.orb, m.aux) for m in mols], 1e-12)
+    plan_s = time.time() - t0
+    Ds = [torch.tensor(W.density(rng, int(oracle.ao_offsets(m.orb)[-1])), device=dev) for m in mols]
+    cs = [torch.tensor(rng.standard_normal(int(oracle.ao_offsets(m.aux)[-1])), device=dev) for m in mols]
+    t0 = time.time()
+    b.bind(Ds, cs)
+    bind_s = time.time() - t0
+    info = b.info()
+    b.execute(2)
+    m2 = event_ms(lambda: b.execute(2))[0]
+    m0 = event_ms(lambda: b.execute(0))[0]
+    m1 = event_ms(lambda: b.execute(1))[0]
+    fl = info["flops"]
+    return dict(workload="16 molecules of 20-400 atoms, orbital 3s2p2d1f1g (K=6/3/1/1/1, 25%% of the orbital shells "
+                         "kept per molecule), aux 8s6p5d4f3g2h1i (K=1), DF-J digest, every class to (gg|i) mixed",
+                screened_triples=info["tasks"], plan_s=round(plan_s, 2), bind_capture_s=round(bind_s, 2),
+                graph_branches_s=round(m2 / 1e3, 3), per_class_s=round(m0 / 1e3, 3),
+                graph_persistent_s=round(m1 / 1e3, 3),
+                frac=dict(graph_branches=round(fl / m2 / 1e6 / FP64_PEAK_GFLOPS, 4),
+                          per_class=round(fl / m0 / 1e6 / FP64_PEAK_GFLOPS, 4),
+                          graph_persistent=round(fl / m1 / 1e6 / FP64_PEAK_GFLOPS, 4)),
+                launches=dict(per_class=int(info["plain_launches"]), graph_branches_kernel_nodes=int(info["branch_kernels"]),
+                              graph_persistent_kernel_nodes=int(info["graph_kernels"]), graph_launches=1),
+                speedup_graph_vs_per_class=round(m0 / m2, 4))
+
+
+def extra_grad(dev):
+    """64-atom DF-J energy E = c^T gamma: forward, gradient (backward), fwd+bwd vs plain DF-J."""
+    import torch
+    import paper_2210_03192_gb300 as lx
+    from paper_2210_03192_gb300 import workloads as W
+    cl = W.cluster64_grad()
+    rng = np.random.default_rng(W.SEED_BASE + 4)
+    plan = lx.DFJPlan(cl.orb, cl.aux, 1e-12, gradient=True)
+    D = torch.tensor(W.density(rng, plan.nao), device=dev)
+    c = torch.tensor(rng.standard_normal(plan.naux_ao), device=dev)
+    gamma = torch.empty(plan.naux_ao, dtype=torch.float64, device=dev)
+    J = torch.empty((plan.nao, plan.nao), dtype=torch.float64, device=dev)
+    grad = torch.empty((plan.natom, 3), dtype=torch.float64, device=dev)
+    plan.energy(D, c)
+    plan.gradient(D, c, grad)
+    fwd = statistics.median(event_ms(lambda: plan.energy(D, c), 2))
+    bwd = statistics.median(event_ms(lambda: plan.gradient(D, c, grad), 2))
+    both = statistics.median(event_ms(lambda: (plan.energy(D, c), plan.gradient(D, c, grad)), 2))
+    plain = statistics.median(event_ms(lambda: plan.execute(D, c, gamma, J), 2))
+    return dict(workload="64-atom jittered grid, orbital 3s2p2d1f1g, aux 8s6p5d4f3g2h, E = c^T gamma, dE/dR [64,3]",
+                screened_triples=plan.ntasks, fwd_ms=round(fwd, 2), bwd_ms=round(bwd, 2), fwd_bwd_ms=round(both, 2),
+                plain_fwd_gamma_J_ms=round(plain, 2), fwd_bwd_over_fwd=round(both / fwd, 3),
+                bwd_frac=round(plan.grad_flops / bwd / 1e6 / FP64_PEAK_GFLOPS, 4),
+                launches=dict(fwd=plan.launches, bwd=plan.grad_launches))
+
+
+EXTRAS = dict(config1=extra_config1, dfj=extra_dfj, batch=extra_batch, grad=extra_grad)
+
+
+def run_extras(args, dev):
+    import torch
+    import paper_2210_03192_gb300 as lx
+    out = {}
+    names = [] if args.extras == "none" else [x for x in args.extras.split(",") if x]
+    g, ms = lx.fp64_rate(1 << 17)
+    out["fp64_peak_measured"] = dict(gflops=round(g, 1), ms=round(ms, 2), frac_of_derived=round(g / FP64_PEAK_GFLOPS, 4),
+                                     method="lx3c_fp64_rate: 8 independent FMA chains per thread, every SM filled, "
+                                            "CUDA events")
+    for n in names:
+        if n not in EXTRAS:
+            raise SystemExit("unknown extra %r (choose from %s)" % (n, ",".join(EXTRAS)))
+        out[n] = with_clocks(dev, lambda: EXTRAS[n](dev))
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -347,7 +519,10 @@ def main():
         c = oracle_sample(classes, args, args.cpu_seconds)
         cpu = {k: c[k] for k in ("value", "unit", "cores", "kind", "sample")}
     value = res["total_int"] / (res["ms"] / 1e3) / 1e9
-    top = sorted(res["table"], key=lambda r: -r["ms"])[:12]
+    top = sorted(res["table"], key=lambda r: -r["ms"])[:8]
+    low = sorted((r for r in res["table"] if sum(r["cls"][:3]) >= 3), key=lambda r: r["frac"])[:5]
+    import torch
+    extras = run_extras(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
     line = dict(
         metric="3c-ERI Gints/s FP64 per (La,Lb,Lc,K)", value=round(value, 4), unit="Gints/s", n_gpus=world,
         steps=args.steps, warmup=args.warmup, ms_per_step=round(res["ms"] / args.steps, 2),
@@ -359,15 +534,17 @@ def main():
         roofline=res["roofline"], cpu_baseline=cpu, clocks=res["clocks"], gpu_launches=res["launches"],
         fp64_tflops_sweep=round(res["total_flops"] / (res["ms"] / 1e3) / 1e12, 4),
         l3_roofline_frac=res["l3_frac"],
-        top_classes=[dict(cls=r["cls"], ms=r["ms"], gints_s=r["gints_s"], frac=r["frac"]) for r in top],
-        per_class=[[*r["cls"], r["ms"], r["gints_s"], r["frac"]] for r in res["table"]],
+        slowest_classes=[[*r["cls"], r["ms"], r["frac"]] for r in top],
+        lowest_frac_l3_classes=[[*r["cls"], r["ms"], r["frac"]] for r in low],
+        class_row="[la, lb, lc, K_ab, ms, FP64 fraction]",
     )
     if "e2e" in res:
         line["e2e"] = res["e2e"]
+    line.update(extras)
     if args.per_class_out:
         with open(args.per_class_out, "w") as f:
             json.dump(res["table"], f)
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, separators=(",", ":")), flush=True)
 
 
 if __name__ == "__main__":

@@ -147,6 +147,17 @@ lx3c_status lx3c_eri3c_host(int64_t orb_nshell, const int32_t* orb_l, const int3
 lx3c_status lx3c_boys(const double* T, int64_t n, int mmax, double* out, void* stream);
 
 /*
+ * Measured FP64 FMA throughput of the current device (not in the paper; the
+ * roofline denominator of the FP64-bound integral kernels): one kernel of
+ * `iters` steps of eight independent FMA chains per thread, every SM filled,
+ * timed with CUDA events on `stream` after a short warm-up launch.
+ * *gflops = 2 * 8 * iters * threads / seconds / 1e9; *ms (may be NULL) = the
+ * timed launch's duration.  Allocates and frees a small device buffer and
+ * synchronises `stream`.  LX3C_EINVAL for iters < 1 or a NULL gflops.
+ */
+lx3c_status lx3c_fp64_rate(int64_t iters, double* gflops, double* ms, void* stream);
+
+/*
  * Algorithmic FP64 floating-point operations (FMA = 2) for one contracted
  * (pair, aux) triple of class (la, lb | lc) with Kab primitive pairs and Kc
  * ket primitives, counted on the FLOP-minimal form of the scheme.
@@ -167,6 +178,26 @@ lx3c_status lx3c_class_flops(int la, int lb, int lc, int Kab, int Kc, int bra_pu
  * Both return LX3C_EINVAL for arguments out of range.
  */
 lx3c_status lx3c_shape_hint(int la, int lb, int lc, int bra_pure, int kab, int kc, int ctas_per_sm);
+
+/*
+ * Accuracy settings (not in the paper), process-wide and thread-safe, read
+ * by every later plan (plans made before the call keep theirs):
+ * lx3c_set_orientation_threshold: HRR (Eq. hrr) moves the recurrence centre's
+ *   quanta to the other centre through AB; when P sits close to the target
+ *   centre this cancels and amplifies FP64 rounding.  A pair keeps one
+ *   orientation when its worst weighted amplification estimate there is at
+ *   most amp_max, otherwise each primitive pair runs its recurrences on its
+ *   more compact centre (a second, transposed launch).  Smaller values split
+ *   more pairs (more accurate, more post-contraction work).  amp_max >= 1,
+ *   or 0 for the default 300; else LX3C_EINVAL.
+ * lx3c_set_compensation: bits selecting compensated (Dot2: TwoProduct by FMA
+ *   and TwoSum) summation in the contracted stages -- bit 0 the n-quantum
+ *   CVRR2 gather (Sec. 2.5.4), bit 1 the ket Cartesian-to-solid-harmonic
+ *   transform; 0 (the default) for plain FMA chains.  bits outside 0..3 give
+ *   LX3C_EINVAL.
+ */
+lx3c_status lx3c_set_orientation_threshold(double amp_max);
+lx3c_status lx3c_set_compensation(int bits);
 
 /*
  * Self-check of the planner's host tables for class (la, lb | lc) (not in the

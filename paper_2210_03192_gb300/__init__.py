@@ -181,18 +181,26 @@ class DFJPlan:
                                         ctypes.c_void_p(grad.data_ptr()), _stream_handle(stream)), "lx3c_dfj_grad")
         return grad
 
-    def execute(self, D, c, gamma=None, J=None, stream=None):
+    def execute(self, D, c, gamma=None, J=None, stream=None, outputs="both"):
+        """gamma and J (outputs="both"), or only one of them ("gamma" / "J"; the
+        other is skipped and returned as None)."""
         torch = _torch()
         for name, t, n in (("D", D, self.nao * self.nao), ("c", c, self.naux_ao)):
             if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
                 raise LibraryError("DFJPlan.execute: %s must be a contiguous float64 CUDA tensor of %d" % (name, n))
-        if gamma is None:
+        if outputs not in ("both", "gamma", "J"):
+            raise LibraryError("DFJPlan.execute: outputs must be 'both', 'gamma' or 'J'")
+        if outputs == "J":
+            gamma = None
+        elif gamma is None:
             gamma = torch.empty(self.naux_ao, dtype=torch.float64, device=D.device)
-        if J is None:
+        if outputs == "gamma":
+            J = None
+        elif J is None:
             J = torch.empty((self.nao, self.nao), dtype=torch.float64, device=D.device)
-        check(_lib.load().lx3c_dfj_execute(self.handle, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(c.data_ptr()),
-                                           ctypes.c_void_p(gamma.data_ptr()), ctypes.c_void_p(J.data_ptr()),
-                                           _stream_handle(stream)), "lx3c_dfj_execute")
+        vp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        check(_lib.load().lx3c_dfj_execute(self.handle, vp(D), vp(c), vp(gamma), vp(J), _stream_handle(stream)),
+              "lx3c_dfj_execute")
         return gamma, J
 
     def groups(self):
@@ -348,6 +356,18 @@ def shape_query(la, lb, lc, kab, kc=1, naux=512, ctas_per_sm=0, bra_pure=True):
     return tuple(int(x) for x in out)
 
 
+def set_orientation_threshold(amp_max=0.0):
+    """Largest weighted HRR amplification a pair keeps unsplit (0: default 300),
+    for later plans (lx3c_set_orientation_threshold)."""
+    check(_lib.load().lx3c_set_orientation_threshold(float(amp_max)), "lx3c_set_orientation_threshold")
+
+
+def set_compensation(bits=0):
+    """Compensated summation in later plans' contracted stages: bit 0 gather,
+    bit 1 ket transform (lx3c_set_compensation)."""
+    check(_lib.load().lx3c_set_compensation(int(bits)), "lx3c_set_compensation")
+
+
 HINTS_GB300 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "shape_hints_gb300.txt")
 
 
@@ -364,6 +384,14 @@ def load_shape_hints(path=HINTS_GB300):
             shape_hint(la, lb, lc, kab, kc, ctas, bool(pure))
             n += 1
     return n
+
+
+def fp64_rate(iters=1 << 16, stream=None):
+    """Measured FP64 FMA rate of the current device: (GFLOP/s, ms) (lx3c_fp64_rate)."""
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    check(_lib.load().lx3c_fp64_rate(int(iters), ctypes.byref(g), ctypes.byref(ms), _stream_handle(stream)),
+          "lx3c_fp64_rate")
+    return g.value, ms.value
 
 
 def class_flops(la, lb, lc, Kab, Kc=1, bra_pure=True):

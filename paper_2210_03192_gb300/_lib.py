@@ -37,6 +37,7 @@ EXPORTS = {
                         [ctypes.c_void_p] * 5 + [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "lx3c_boys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "lx3c_fp64_rate": (ctypes.c_int, [ctypes.c_int64, c_f64p, c_f64p, ctypes.c_void_p]),
     "lx3c_class_flops": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, c_f64p]),
     "lx3c_solid_harmonics": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
@@ -59,6 +60,8 @@ EXPORTS = {
     "lx3c_cvrr2_expansion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "lx3c_shape_hint": (ctypes.c_int, [ctypes.c_int] * 7),
+    "lx3c_set_orientation_threshold": (ctypes.c_int, [ctypes.c_double]),
+    "lx3c_set_compensation": (ctypes.c_int, [ctypes.c_int]),
     "lx3c_class_tables_check": (ctypes.c_int, [ctypes.c_int] * 4),
     "lx3c_shape_query": (ctypes.c_int, [ctypes.c_int] * 6 + [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
 }

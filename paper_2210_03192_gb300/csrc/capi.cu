@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -97,14 +98,6 @@ lx3c_status device_state(DevState** out) {
   return LX3C_OK;
 }
 
-template <class T>
-size_t append(std::vector<char>& blob, const std::vector<T>& v) {
-  size_t off = (blob.size() + 15) & ~size_t(15);
-  blob.resize(off + v.size() * sizeof(T) + 16);
-  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
-  return off;
-}
-
 lx3c_status device_class(DevState* s, const ClassTables& ct, DevClass** out) {
   std::lock_guard<std::mutex> lk(g_mu);
   auto key = std::make_tuple(ct.la, ct.lb, ct.lc, ct.bra_pure);
@@ -113,33 +106,12 @@ lx3c_status device_class(DevState* s, const ClassTables& ct, DevClass** out) {
     *out = &it->second;
     return LX3C_OK;
   }
-  std::vector<char> blob;
-  size_t o_v = append(blob, ct.vtab), o_w = append(blob, ct.wtab), o_a = append(blob, ct.atab),
-         o_gp = append(blob, ct.gptr), o_gt = append(blob, ct.gterm), o_gd = append(blob, ct.gdst),
-         o_pal = append(blob, ct.pal), o_kp = append(blob, ct.kptr), o_ke = append(blob, ct.kent),
-         o_h = append(blob, ct.htab), o_bap = append(blob, ct.baptr), o_bae = append(blob, ct.baent),
-         o_bbp = append(blob, ct.bbptr), o_bbe = append(blob, ct.bbent), o_ge = append(blob, ct.gell),
-         o_gs = append(blob, ct.gslice);
+  size_t offs[16];
+  std::vector<char> blob = class_blob(ct, offs);
   DevClass dc;
   CUDA_TRY(cudaMalloc(&dc.blob, blob.size()));
   CUDA_TRY(cudaMemcpy(dc.blob, blob.data(), blob.size(), cudaMemcpyHostToDevice));
-  char* b = (char*)dc.blob;
-  dc.vtab = (const uint4*)(b + o_v);
-  dc.wtab = (const int4*)(b + o_w);
-  dc.atab = (const unsigned*)(b + o_a);
-  dc.gptr = (const int*)(b + o_gp);
-  dc.gterm = (const unsigned*)(b + o_gt);
-  dc.gdst = (const int*)(b + o_gd);
-  dc.pal = (const double*)(b + o_pal);
-  dc.kptr = (const int*)(b + o_kp);
-  dc.kent = (const int2*)(b + o_ke);
-  dc.htab = (const int4*)(b + o_h);
-  dc.baptr = (const int*)(b + o_bap);
-  dc.baent = (const int2*)(b + o_bae);
-  dc.bbptr = (const int*)(b + o_bbp);
-  dc.bbent = (const int2*)(b + o_bbe);
-  dc.gell = (const unsigned*)(b + o_ge);
-  dc.gslice = (const int2*)(b + o_gs);
+  class_blob_pointers(dc, dc.blob, offs);
   auto r = s->classes.emplace(key, dc);
   *out = &r.first->second;
   return LX3C_OK;
@@ -156,10 +128,49 @@ const double* dev_boys_mid(const DevState* s) { return s->boys_mid; }
 int dev_nsm(const DevState* s) { return s->nsm; }
 int dev_smem(const DevState* s) { return s->smem_per_sm; }
 
-int fill_class_desc(ClassDesc& d, const ClassTables& ct, const DevClass& dc, const DevState* ds, int orient,
-                    int kmax, int Kab_rec, int Kc, long long naux_for_shape) {
-  LaunchShape sh = choose_shape(ct, kmax, Kc, naux_for_shape, ds->smem_per_sm);
-  if (sh.smem_bytes < 0 || sh.smem_bytes > 232448) return -1;
+namespace {
+template <class T>
+size_t append(std::vector<char>& blob, const std::vector<T>& v) {
+  size_t off = (blob.size() + 15) & ~size_t(15);
+  blob.resize(off + v.size() * sizeof(T) + 16);
+  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+}  // namespace
+
+std::vector<char> class_blob(const ClassTables& ct, size_t f[16]) {
+  std::vector<char> blob;
+  f[0] = append(blob, ct.vtab); f[1] = append(blob, ct.wtab); f[2] = append(blob, ct.atab);
+  f[3] = append(blob, ct.gptr); f[4] = append(blob, ct.gterm); f[5] = append(blob, ct.gdst);
+  f[6] = append(blob, ct.pal); f[7] = append(blob, ct.kptr); f[8] = append(blob, ct.kent);
+  f[9] = append(blob, ct.htab); f[10] = append(blob, ct.baptr); f[11] = append(blob, ct.baent);
+  f[12] = append(blob, ct.bbptr); f[13] = append(blob, ct.bbent); f[14] = append(blob, ct.gell);
+  f[15] = append(blob, ct.gslice);
+  return blob;
+}
+
+void class_blob_pointers(DevClass& dc, const void* dev_blob, const size_t f[16]) {
+  const char* b = (const char*)dev_blob;
+  dc.vtab = (const uint4*)(b + f[0]);
+  dc.wtab = (const int4*)(b + f[1]);
+  dc.atab = (const unsigned*)(b + f[2]);
+  dc.gptr = (const int*)(b + f[3]);
+  dc.gterm = (const unsigned*)(b + f[4]);
+  dc.gdst = (const int*)(b + f[5]);
+  dc.pal = (const double*)(b + f[6]);
+  dc.kptr = (const int*)(b + f[7]);
+  dc.kent = (const int2*)(b + f[8]);
+  dc.htab = (const int4*)(b + f[9]);
+  dc.baptr = (const int*)(b + f[10]);
+  dc.baent = (const int2*)(b + f[11]);
+  dc.bbptr = (const int*)(b + f[12]);
+  dc.bbent = (const int2*)(b + f[13]);
+  dc.gell = (const unsigned*)(b + f[14]);
+  dc.gslice = (const int2*)(b + f[15]);
+}
+
+void fill_desc_common(ClassDesc& d, const ClassTables& ct, const DevClass& dc, const double* boys_tab,
+                      const double* boys_mid, int orient, int kmax, int Kab_rec, int Kc, const LaunchShape& sh) {
   std::memset(&d, 0, sizeof(d));
   d.la = ct.la; d.lb = ct.lb; d.lc = ct.lc; d.Lab = ct.la + ct.lb; d.L = ct.la + ct.lb + ct.lc;
   d.bra_pure = ct.bra_pure;
@@ -182,9 +193,17 @@ int fill_class_desc(ClassDesc& d, const ClassTables& ct, const DevClass& dc, con
   d.gdst = dc.gdst; d.pal = dc.pal; d.kptr = dc.kptr; d.kent = dc.kent; d.htab = dc.htab;
   d.gell = dc.gell; d.gslice = dc.gslice;
   d.baptr = dc.baptr; d.baent = dc.baent; d.bbptr = dc.bbptr; d.bbent = dc.bbent;
-  d.boys_tab = ds->boys_tab; d.boys_mid = ds->boys_mid; d.boys_cL = boys_large_const(d.L);
+  d.boys_tab = boys_tab; d.boys_mid = boys_mid; d.boys_cL = boys_large_const(d.L);
+  d.comp = compensation_bits();
   fill_layout(d, ct, sh);
   d.nchunk = (d.K + d.G - 1) / d.G;
+}
+
+int fill_class_desc(ClassDesc& d, const ClassTables& ct, const DevClass& dc, const DevState* ds, int orient,
+                    int kmax, int Kab_rec, int Kc, long long naux_for_shape) {
+  LaunchShape sh = choose_shape(ct, kmax, Kc, naux_for_shape, ds->smem_per_sm);
+  if (sh.smem_bytes < 0 || sh.smem_bytes > 232448) return -1;
+  fill_desc_common(d, ct, dc, ds->boys_tab, ds->boys_mid, orient, kmax, Kab_rec, Kc, sh);
   return sh.smem_bytes;
 }
 
@@ -203,9 +222,17 @@ namespace lx3c {
 // amp is at most kAmpMax; otherwise every primitive pair runs on its more
 // compact centre (two launches, the second accumulating transposed).
 // Without HRR (lb = 0) the caller's orientation is always kept.
+namespace {
+std::atomic<double> g_amp_max{kDefaultAmpMax};
+std::atomic<int> g_comp_bits{0};
+}  // namespace
+
+double orientation_amp_max() { return g_amp_max.load(); }
+int compensation_bits() { return g_comp_bits.load(); }
+
 void split_orientation(const lx3c_basis* orb, int a, int b, int la, int lb, std::vector<int>& primA,
                        std::vector<int>& primB) {
-  const double kAmpMax = 300.0;
+  const double kAmpMax = orientation_amp_max();
   const int Ka = orb->k[a], Kb = orb->k[b];
   const double* A = &orb->xyz[3 * a];
   const double* B = &orb->xyz[3 * b];
@@ -619,6 +646,19 @@ lx3c_status lx3c_class_tables_check(int la, int lb, int lc, int bra_pure) {
   } catch (std::exception& e) {
     return fail(LX3C_ENOTSUP, e.what());
   }
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_set_orientation_threshold(double amp_max) {
+  if (!(amp_max == 0.0 || (amp_max >= 1.0 && std::isfinite(amp_max))))
+    return fail(LX3C_EINVAL, "set_orientation_threshold: amp_max must be 0 (default) or a finite value >= 1");
+  g_amp_max.store(amp_max == 0.0 ? kDefaultAmpMax : amp_max);
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_set_compensation(int bits) {
+  if (bits < 0 || bits > 3) return fail(LX3C_EINVAL, "set_compensation: bits must be in 0..3");
+  g_comp_bits.store(bits);
   return LX3C_OK;
 }
 

@@ -19,6 +19,7 @@ constexpr int kBoysPerUnit = 8;          // intervals per unit of T (width 1/8)
 constexpr int kBoysNInt = 117 * kBoysPerUnit;
 constexpr double kBoysTMax = 117.0;
 constexpr int kBoysDeg = 7;              // degree of the interpolating polynomial (Sec. 2.5.2)
+constexpr double kDefaultAmpMax = 300.0; // orientation: largest weighted HRR amplification kept unsplit
 
 // Pair record fields (doubles), one record per primitive pair (a_i, b_j):
 //   0 gamma = za+zb
@@ -89,6 +90,9 @@ struct ClassDesc {
   int pair_base, aux_base, ab_base;
   Buf V, W, F, P, Gb, H[kMaxLev + 1], BA, BB, OUT;
   int smem_doubles;
+  // compensated (Dot2) summation in the contracted stages: bit 0 the CVRR2
+  // gather, bit 1 the ket transform
+  int comp;
   // data
   const double* pairrec;   // [npair][Kab][kPairRec]
   const double* pairab;    // [npair][3]  AB = A - B
@@ -204,6 +208,16 @@ void set_last_error(const std::string& msg);
 // -1 if the class does not fit.
 int fill_class_desc(ClassDesc& d, const ClassTables& ct, const DevClass& dc, const DevState* ds, int orient,
                     int kmax, int Kab_rec, int Kc, long long naux_for_shape);
+struct LaunchShape;
+// The shape-independent part of that fill plus the layout for shape sh, with
+// the class tables at dc and the Boys table at boys_tab / boys_mid (shared by
+// the planned and the allocation-free paths).
+void fill_desc_common(ClassDesc& d, const ClassTables& ct, const DevClass& dc, const double* boys_tab,
+                      const double* boys_mid, int orient, int kmax, int Kab_rec, int Kc, const LaunchShape& sh);
+// Device pointers of every class table inside one uploaded blob laid out by
+// class_blob (same offsets on host and device).
+std::vector<char> class_blob(const ClassTables& ct, size_t offs[16]);
+void class_blob_pointers(DevClass& dc, const void* dev_blob, const size_t offs[16]);
 
 // planner entry points (plan.cu)
 const ClassTables& class_tables(int la, int lb, int lc, int bra_pure);
@@ -234,7 +248,10 @@ LaunchShape choose_shape_for(const ClassTables& ct, int Kab, int Kc, long long n
 void set_shape_hint(int la, int lb, int lc, int bra_pure, int Kab, int Kc, int ctas);
 void fill_layout(ClassDesc& d, const ClassTables& ct, const LaunchShape& s);
 
-// Orientation split of one pair's primitive pairs (capi.cu).
+// Process-wide accuracy settings (capi.cu): the orientation split's
+// amplification threshold and the compensated-summation bits of new plans.
+double orientation_amp_max();
+int compensation_bits();
 }  // namespace lx3c
 
 // Shell table, host copy plus device SoA copy (opaque in the C ABI).

@@ -9,9 +9,10 @@
 
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lx3c.h"
@@ -66,8 +67,9 @@ std::vector<double> g_na_boys, g_na_mid;
 // path's rule (lx3c_eri3c_plan): a pair keeps one orientation when its worst
 // weighted HRR amplification there is at most amp_max, otherwise each
 // primitive pair runs on its more compact centre.  Sub-pair p of list o holds
-// its primitive indices at prim[o][p*kab ...]; list 1 always accumulates onto
-// list 0's store.
+// its primitive indices at prim[o][p*kab ...].  A sub-pair with no primitive
+// pairs is skipped by the integral kernel; list 1 accumulates onto list 0's
+// store only where list 0 has primitive pairs for that pair.
 __global__ void noalloc_orient(const int32_t* __restrict__ pairs, long long npair, int la, int lb, int ka, int kb,
                                const int64_t* __restrict__ off, const double* __restrict__ xyz,
                                const double* __restrict__ exps, const double* __restrict__ coefs, double amp_max,
@@ -105,15 +107,32 @@ __global__ void noalloc_orient(const int32_t* __restrict__ pairs, long long npai
       else prim[p * kab + na++] = ia * kb + ib;
     }
   sub[p] = int4{(int)p, (int)(p * kab), na, 0};
-  sub[npair + p] = int4{(int)p, (int)(p * kab), nb, 1};
+  sub[npair + p] = int4{(int)p, (int)(p * kab), nb, na > 0 ? 1 : 0};
 }
 
-template <class T>
-size_t put(std::vector<char>& blob, const std::vector<T>& v) {
-  size_t o = (blob.size() + 15) & ~size_t(15);
-  blob.resize(o + v.size() * sizeof(T) + 16);
-  if (!v.empty()) std::memcpy(blob.data() + o, v.data(), v.size() * sizeof(T));
-  return o;
+// Host copy of both orientations' class tables, one blob per class, made on
+// first use and kept until process exit.
+struct NaBlob {
+  std::vector<char> bytes;
+  size_t base[2] = {0, 0};
+  size_t offs[2][16] = {};
+};
+
+const NaBlob& na_blob(int la, int lb, int lc, int bra_pure, int split) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, NaBlob> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(la, lb, lc, bra_pure);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  NaBlob nb;
+  for (int o = 0; o < 1 + split; ++o) {
+    std::vector<char> part = class_blob(class_tables(o ? lb : la, o ? la : lb, lc, bra_pure), nb.offs[o]);
+    nb.base[o] = (nb.bytes.size() + 255) & ~size_t(255);
+    nb.bytes.resize(nb.base[o] + part.size());
+    std::memcpy(nb.bytes.data() + nb.base[o], part.data(), part.size());
+  }
+  return cache.emplace(key, std::move(nb)).first->second;
 }
 
 }  // namespace
@@ -172,28 +191,21 @@ extern "C" lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb
   double* auxc = (double*)(base + kOffAuxC);
   int4* sub = (int4*)(base + kOffSub);
   int* prim = (int*)(base + kOffPrim);
-  // class tables of both orientations, packed into the table region
+  // class tables of both orientations, packed into the table region from a
+  // host copy kept for the life of the process (the copy's source outlives
+  // the call)
   const ClassTables* cts[2];
+  const NaBlob* nb = nullptr;
   try {
     cts[0] = &class_tables(la, lb, lc, bra_pure ? 1 : 0);
     cts[1] = &class_tables(lb, la, lc, bra_pure ? 1 : 0);
+    nb = &na_blob(la, lb, lc, bra_pure ? 1 : 0, split);
   } catch (std::exception& ex) {
     return na_fail(LX3C_ENOTSUP, ex.what());
   }
-  std::vector<char> blob;
-  size_t offs[2][16];
-  for (int o = 0; o < 1 + split; ++o) {
-    const ClassTables& ct = *cts[o];
-    size_t* f = offs[o];
-    f[0] = put(blob, ct.vtab); f[1] = put(blob, ct.wtab); f[2] = put(blob, ct.atab); f[3] = put(blob, ct.gptr);
-    f[4] = put(blob, ct.gterm); f[5] = put(blob, ct.gdst); f[6] = put(blob, ct.pal); f[7] = put(blob, ct.kptr);
-    f[8] = put(blob, ct.kent); f[9] = put(blob, ct.htab); f[10] = put(blob, ct.baptr); f[11] = put(blob, ct.baent);
-    f[12] = put(blob, ct.bbptr); f[13] = put(blob, ct.bbent); f[14] = put(blob, ct.gell);
-    f[15] = put(blob, ct.gslice);
-  }
-  if (blob.size() > kTableBytes) return na_fail(LX3C_ENOTSUP, "class tables exceed the scratch table region");
+  if (nb->bytes.size() > kTableBytes) return na_fail(LX3C_ENOTSUP, "class tables exceed the scratch table region");
   unsigned char* tb = base + kOffTables;
-  e = cudaMemcpyAsync(tb, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
+  e = cudaMemcpyAsync(tb, nb->bytes.data(), nb->bytes.size(), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return na_fail(LX3C_ECUDA, cudaGetErrorString(e));
   DevBasis orb{nullptr, nullptr, orb_off, orb_xyz, orb_exps, orb_coefs};
   DevBasis aux{nullptr, nullptr, aux_off, aux_xyz, aux_exps, aux_coefs};
@@ -201,7 +213,7 @@ extern "C" lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb
   if (e == cudaSuccess) e = launch_aux_precompute(aux, auxs, naux, kc, auxrec, auxc, st);
   if (e == cudaSuccess) {
     noalloc_orient<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pairs, npair, la, lb, ka, kb, orb_off, orb_xyz,
-                                                                     orb_exps, orb_coefs, 300.0, sub, prim);
+                                                                     orb_exps, orb_coefs, orientation_amp_max(), sub, prim);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return na_fail(LX3C_ECUDA, cudaGetErrorString(e));
@@ -209,37 +221,12 @@ extern "C" lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb
     const ClassTables& ct = *cts[o];
     LaunchShape sh = choose_shape(ct, kab, kc, naux, smem);
     if (sh.smem_bytes < 0 || sh.smem_bytes > 232448) return na_fail(LX3C_ENOTSUP, "class does not fit in shared memory");
+    DevClass dc;
+    class_blob_pointers(dc, tb + nb->base[o], nb->offs[o]);
     ClassDesc d;
-    std::memset(&d, 0, sizeof(d));
-    const int l1 = o ? lb : la, l2 = o ? la : lb;
-    d.la = l1; d.lb = l2; d.lc = lc; d.Lab = l1 + l2; d.L = l1 + l2 + lc; d.bra_pure = bra_pure ? 1 : 0;
-    d.ncA = ct.ncA; d.ncB = ct.ncB; d.ncc = ct.ncc;
-    d.nA = ct.nA; d.nB = ct.nB; d.nC = ct.nC; d.nblk = d.nA * d.nB * d.nC;
-    d.orient = o;
-    d.onA = o ? ct.nB : ct.nA;
-    d.onB = o ? ct.nA : ct.nB;
-    d.Kab = kab; d.Kc = kc; d.K = kab * kc; d.Kab_rec = kab;
-    d.NV = ct.NV; d.NW = ct.NW; d.NF = ct.NF; d.NACC = ct.NACC;
-    for (int q = 0; q <= d.Lab; ++q) d.vlev_start[q] = ct.vlev_start[q];
-    d.nW = ct.NW;
-    d.ngt = ct.nkrow * ct.ncc;
-    d.nkrow = ct.nkrow;
-    for (int j = 0; j <= l2; ++j) d.hrows[j] = ct.hrows[j];
-    for (int j = 0; j <= l2 + 1; ++j) d.hstart[j] = ct.hstart[j];
-    d.nbA = ct.nbA; d.nbB = ct.nbB;
-    const size_t* f = offs[o];
-    d.vtab = (const uint4*)(tb + f[0]); d.wtab = (const int4*)(tb + f[1]); d.atab = (const unsigned*)(tb + f[2]);
-    d.gptr = (const int*)(tb + f[3]); d.gterm = (const unsigned*)(tb + f[4]); d.gdst = (const int*)(tb + f[5]);
-    d.pal = (const double*)(tb + f[6]); d.kptr = (const int*)(tb + f[7]); d.kent = (const int2*)(tb + f[8]);
-    d.htab = (const int4*)(tb + f[9]); d.baptr = (const int*)(tb + f[10]); d.baent = (const int2*)(tb + f[11]);
-    d.bbptr = (const int*)(tb + f[12]); d.bbent = (const int2*)(tb + f[13]);
-    d.gell = (const unsigned*)(tb + f[14]); d.gslice = (const int2*)(tb + f[15]);
-    d.boys_tab = (const double*)(base + kOffBoys);
-    d.boys_mid = (const double*)(base + kOffBoysMid);
-    d.boys_cL = boys_large_const(d.L);
+    fill_desc_common(d, ct, dc, (const double*)(base + kOffBoys), (const double*)(base + kOffBoysMid), o, kab, kab,
+                     kc, sh);
     d.npair = npair; d.naux = naux;
-    fill_layout(d, ct, sh);
-    d.nchunk = (d.K + d.G - 1) / d.G;
     d.ntile_aux = (int)((naux + d.T - 1) / d.T);
     d.nsub = npair;
     d.ntiles = npair * d.ntile_aux;
