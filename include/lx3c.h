@@ -59,6 +59,7 @@ typedef struct lx3c_basis lx3c_basis;
 typedef struct lx3c_plan lx3c_plan;
 typedef struct lx3c_dfj lx3c_dfj;
 typedef struct lx3c_batch lx3c_batch;
+typedef struct lx3c_metric lx3c_metric;
 
 /* Thread-local description of the last failure in this thread. */
 const char* lx3c_last_error(void);
@@ -278,6 +279,48 @@ lx3c_status lx3c_dfj_info(const lx3c_dfj* plan, double* out, int n);
 lx3c_status lx3c_dfj_group(const lx3c_dfj* plan, int gi, int32_t* info, int32_t* pairs, int32_t* counts,
                            int32_t* auxs);
 void lx3c_dfj_destroy(lx3c_dfj* plan);
+
+/*
+ * Density-fitting metric and solve.  The paper's DF-J (Sec. 1: density
+ * fitting of the Coulomb operator; Sec. 4: DF-J with a J-fitting auxiliary
+ * basis) fits the density as c = V^{-1} gamma with the Coulomb metric
+ * V_PQ = (P|Q) of the auxiliary basis, then forms J_{mu nu} = sum_P (mu nu|P) c_P.
+ *
+ * lx3c_metric_plan: plan V for an aux basis (all shells, any mix of l <=
+ *   LX3C_LMAX_AUX and K).  (P|Q) is evaluated by the class kernels as the
+ *   3-centre integral (P 1|Q) whose second bra function is the constant 1
+ *   (an s Gaussian with exponent 0), one (l_P 0 | l_Q) class launch per pair
+ *   of (l, K) shell groups.  Setup; synchronises `stream`.
+ * lx3c_metric_execute: V (device, naux_ao x naux_ao row-major, AO order =
+ *   shell order, components m = -l..l) receives every element, both
+ *   triangles (V is symmetric).  Asynchronous on `stream`.
+ * lx3c_metric_info: out[0..5] = naux_ao, shell groups, class launches,
+ *   kernel launches per execute, algorithmic FP64 flops per execute, shell
+ *   pairs.
+ * lx3c_cholesky: in-place Cholesky V = L L^T of the symmetric positive
+ *   definite A (device, n x n row-major, leading dimension lda >= n), reading
+ *   and writing only the lower triangle (the strictly upper triangle is left
+ *   as it was).  Blocked right-looking, 64-wide panels, FP64 throughout.
+ *   info (device int32, may be NULL) is set to 0, or to the 1-based index of
+ *   the first non-positive pivot (the factor then holds NaN from there on).
+ *   Asynchronous on `stream`; LX3C_EINVAL for n < 1, lda < n or a NULL A.
+ * lx3c_cholesky_solve: B <- (L L^T)^{-1} B with L from lx3c_cholesky and B
+ *   (device, n x nrhs row-major, the nrhs right-hand sides contiguous per
+ *   row) overwritten.  Asynchronous on `stream`.
+ * lx3c_dfj_coulomb: the whole DF-J Coulomb build from a DF-J plan (screened
+ *   integrals, lx3c_dfj_plan) and the metric's Cholesky factor L (lda >=
+ *   naux_ao): gamma = sum (mu nu|P) D_{mu nu} (device, naux_ao out),
+ *   c = V^{-1} gamma (device, naux_ao out), J = sum_P (mu nu|P) c_P (device,
+ *   nao x nao out).  Two integral passes and one solve; asynchronous.
+ */
+lx3c_status lx3c_metric_plan(lx3c_metric** out, const lx3c_basis* aux, void* stream);
+lx3c_status lx3c_metric_execute(lx3c_metric* plan, double* V, void* stream);
+lx3c_status lx3c_metric_info(const lx3c_metric* plan, double* out, int n);
+void lx3c_metric_destroy(lx3c_metric* plan);
+lx3c_status lx3c_cholesky(double* A, int64_t n, int64_t lda, int32_t* info, void* stream);
+lx3c_status lx3c_cholesky_solve(const double* L, int64_t n, int64_t lda, double* B, int64_t nrhs, void* stream);
+lx3c_status lx3c_dfj_coulomb(lx3c_dfj* plan, const double* L, int64_t lda, const double* D, double* gamma,
+                             double* c, double* J, void* stream);
 
 /*
  * Batched uneven workload (not in the paper; the paper launches one class per

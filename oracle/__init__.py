@@ -15,8 +15,10 @@ Pieces (each cites the passage of the paper it follows):
   quadrature.py         brute-force quadrature of the defining integral, used
                         only to pin md3c on tiny inputs
   this file             contraction/transform drivers, DF-J gamma and J
-                        (Sec. 3: integral digestion into a DF-J build), and
-                        the nuclear gradient of E = c^T gamma.
+                        (Sec. 3: integral digestion into a DF-J build), the
+                        density-fitting metric V_PQ = (P|Q) and the fitted
+                        density c = V^{-1} gamma (Sec. 1), and the nuclear
+                        gradient of E = c^T gamma.
 
 All functions take plain numpy arrays.  A basis is any object with attributes
   l[nsh] int, k[nsh] int (primitives per shell), off[nsh] int (first primitive),
@@ -260,6 +262,44 @@ def dfj(orb, aux, D, c, tasks=None, extended=False, mode="double"):
         if i != j:
             J[sj, si] += Jb.T
     return gamma, J
+
+
+# --------------------------------------------------------------------------
+# Density-fitting metric V_PQ = (P|Q) and the fitted density (Sec. 1, 4)
+# --------------------------------------------------------------------------
+
+def unit_shell_basis(aux):
+    """aux's shells followed by the constant function 1 = exp(-0 r^2) (an s
+    shell with exponent 0 and coefficient 1), so that the 3-centre integral
+    (P 1|Q) is the 2-centre Coulomb integral (P|Q)."""
+    from types import SimpleNamespace
+    k = np.r_[np.asarray(aux.k, np.int32), 1]
+    off = np.zeros(len(k), np.int64)
+    off[1:] = np.cumsum(k)[:-1]
+    return SimpleNamespace(l=np.r_[np.asarray(aux.l, np.int32), 0], k=k, off=off,
+                           xyz=np.vstack([np.asarray(aux.xyz, float).reshape(-1, 3), np.zeros((1, 3))]),
+                           exps=np.r_[np.asarray(aux.exps, float), 0.0], coefs=np.r_[np.asarray(aux.coefs, float), 1.0])
+
+
+def metric(aux, mode="double"):
+    """V[naux_ao, naux_ao], V_PQ = (P|Q) = int int P(r1) |r1 - r2|^-1 Q(r2),
+    all shells solid harmonic, AO order = shell order."""
+    bra = unit_shell_basis(aux)
+    unit = len(aux.l)
+    ns = len(aux.l)
+    P, Q = np.meshgrid(np.arange(ns), np.arange(ns), indexing="ij")
+    pairs = np.stack([P.ravel(), np.full(P.size, unit)], axis=1)
+    blocks = eri3c_triples(bra, aux, pairs, Q.ravel(), bra_pure=True, mode=mode)
+    aq = ao_offsets(aux)
+    V = np.zeros((int(aq[-1]), int(aq[-1])))
+    for (p, q), X in zip(zip(P.ravel(), Q.ravel()), blocks):
+        V[aq[p]:aq[p + 1], aq[q]:aq[q + 1]] = X[:, 0, :]
+    return V
+
+
+def fitted_density(V, gamma):
+    """c = V^{-1} gamma (a library linear solve on the oracle's metric)."""
+    return np.linalg.solve(V, gamma)
 
 
 # --------------------------------------------------------------------------

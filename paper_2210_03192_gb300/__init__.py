@@ -23,7 +23,7 @@ from . import _lib
 from ._lib import LibraryError, check, ptr
 from . import workloads  # noqa: F401  (seeded input generators)
 
-__all__ = ["DeviceBasis", "Eri3cPlan", "DFJPlan", "DFJEnergy", "Batch", "eri3c", "eri3c_host", "boys", "class_flops", "solid_harmonics",
+__all__ = ["DeviceBasis", "Eri3cPlan", "DFJPlan", "DFJEnergy", "Batch", "MetricPlan", "cholesky", "cholesky_solve", "eri3c", "eri3c_host", "boys", "class_flops", "solid_harmonics",
            "cvrr2_expansion", "LibraryError", "workloads"]
 
 
@@ -203,6 +203,19 @@ class DFJPlan:
               "lx3c_dfj_execute")
         return gamma, J
 
+    def coulomb(self, L, D, stream=None):
+        """DF-J Coulomb build with the metric's Cholesky factor L:
+        gamma, c = V^{-1} gamma and J (lx3c_dfj_coulomb)."""
+        torch = _torch()
+        gamma = torch.empty(self.naux_ao, dtype=torch.float64, device=D.device)
+        c = torch.empty(self.naux_ao, dtype=torch.float64, device=D.device)
+        J = torch.empty((self.nao, self.nao), dtype=torch.float64, device=D.device)
+        check(_lib.load().lx3c_dfj_coulomb(self.handle, ctypes.c_void_p(L.data_ptr()), L.stride(0),
+                                           ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(gamma.data_ptr()),
+                                           ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(J.data_ptr()),
+                                           _stream_handle(stream)), "lx3c_dfj_coulomb")
+        return gamma, c, J
+
     def groups(self):
         """Screened task list: list of dicts (class, pairs[n,2], counts[n], auxs[m])."""
         L = _lib.load()
@@ -233,6 +246,65 @@ class DFJPlan:
         if h is not None and h.value and _lib._lib is not None:
             _lib._lib.lx3c_dfj_destroy(h)
             self.handle = None
+
+
+class MetricPlan:
+    """Coulomb metric V_PQ = (P|Q) of an aux basis (lx3c_metric)."""
+
+    def __init__(self, aux, stream=None):
+        L = _lib.load()
+        self.aux = aux if isinstance(aux, DeviceBasis) else DeviceBasis(aux, stream)
+        self.handle = ctypes.c_void_p()
+        check(L.lx3c_metric_plan(ctypes.byref(self.handle), self.aux.handle, _stream_handle(stream)),
+              "lx3c_metric_plan")
+        info = np.zeros(6)
+        check(L.lx3c_metric_info(self.handle, ptr(info), 6), "lx3c_metric_info")
+        self.naux_ao, self.groups, self.class_launches, self.launches = (int(x) for x in info[:4])
+        self.flops = float(info[4])
+
+    def execute(self, V=None, stream=None):
+        torch = _torch()
+        if V is None:
+            V = torch.empty((self.naux_ao, self.naux_ao), dtype=torch.float64, device="cuda")
+        if V.dtype != torch.float64 or not V.is_cuda or not V.is_contiguous() or V.numel() != self.naux_ao ** 2:
+            raise LibraryError("MetricPlan.execute: V must be a contiguous float64 CUDA tensor [%d, %d]"
+                               % (self.naux_ao, self.naux_ao))
+        check(_lib.load().lx3c_metric_execute(self.handle, ctypes.c_void_p(V.data_ptr()), _stream_handle(stream)),
+              "lx3c_metric_execute")
+        return V
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.lx3c_metric_destroy(h)
+            self.handle = None
+
+
+def cholesky(A, stream=None):
+    """In-place lower Cholesky factor of the symmetric positive definite CUDA
+    float64 matrix A (lx3c_cholesky); returns (A, info) with info the 1-based
+    first non-positive pivot or 0 (reading info synchronises)."""
+    torch = _torch()
+    n = A.shape[0]
+    if A.dtype != torch.float64 or not A.is_cuda or A.dim() != 2 or A.shape[1] < n or A.stride(1) != 1:
+        raise LibraryError("cholesky: A must be a row-major float64 CUDA matrix")
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    check(_lib.load().lx3c_cholesky(ctypes.c_void_p(A.data_ptr()), n, A.stride(0), ctypes.c_void_p(info.data_ptr()),
+                                    _stream_handle(stream)), "lx3c_cholesky")
+    return A, int(info.item())
+
+
+def cholesky_solve(L, B, stream=None):
+    """B <- (L L^T)^{-1} B in place (lx3c_cholesky_solve); B is [n] or [n, nrhs]."""
+    torch = _torch()
+    n = L.shape[0]
+    if B.dtype != torch.float64 or not B.is_cuda or not B.is_contiguous() or B.shape[0] != n:
+        raise LibraryError("cholesky_solve: B must be a contiguous float64 CUDA tensor with %d rows" % n)
+    nrhs = 1 if B.dim() == 1 else B.shape[1]
+    check(_lib.load().lx3c_cholesky_solve(ctypes.c_void_p(L.data_ptr()), n, L.stride(0),
+                                          ctypes.c_void_p(B.data_ptr()), nrhs, _stream_handle(stream)),
+          "lx3c_cholesky_solve")
+    return B
 
 
 class Batch:

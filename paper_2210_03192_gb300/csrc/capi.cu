@@ -347,7 +347,18 @@ lx3c_status lx3c_basis_create(lx3c_basis** out, int64_t nshell, const int32_t* l
       return fail(LX3C_EINVAL, "basis_create: exponent must be finite and > 0");
     if (!std::isfinite(b->coefs[i])) return fail(LX3C_EINVAL, "basis_create: non-finite coefficient");
   }
-  cudaStream_t st = (cudaStream_t)stream;
+  lx3c_status rc = basis_upload(b.get(), (cudaStream_t)stream);
+  if (rc) return rc;
+  *out = b.release();
+  return LX3C_OK;
+}
+
+}  // extern "C"
+
+namespace lx3c {
+
+lx3c_status basis_upload(lx3c_basis* b, cudaStream_t st) {
+  const int64_t nshell = b->nshell, np = b->nprim;
   size_t n = (size_t)std::max<int64_t>(nshell, 1), npp = (size_t)std::max<int64_t>(np, 1);
   CUDA_TRY(cudaMalloc(&b->d_l, n * 4));
   CUDA_TRY(cudaMalloc(&b->d_k, n * 4));
@@ -366,9 +377,12 @@ lx3c_status lx3c_basis_create(lx3c_basis** out, int64_t nshell, const int32_t* l
     CUDA_TRY(cudaMemcpyAsync(b->d_coefs, b->coefs.data(), np * 8, cudaMemcpyHostToDevice, st));
   }
   CUDA_TRY(cudaStreamSynchronize(st));
-  *out = b.release();
   return LX3C_OK;
 }
+
+}  // namespace lx3c
+
+extern "C" {
 
 void lx3c_plan_destroy(lx3c_plan* p) {
   if (!p) return;

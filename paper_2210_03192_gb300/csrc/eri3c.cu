@@ -660,6 +660,22 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       __syncthreads();
       cur = d.BB;
     }
+    if (d.digest == 3) {
+      // ---- matrix store (2-centre metric (P|Q) = (P 1|Q), nB = 1): element
+      // (t, A, C) of the tile goes to out[(ao_pair + A) * ldD + ao_ket + C]
+      const int4 pao = __ldg(d.pair_ao + pair);
+      const int nA = d.onA, nC = d.nC, nAC = nA * nC;
+      FDiv fAC, fC;
+      fAC.init(nAC);
+      fC.init(nC);
+      const unsigned n = (unsigned)(tv * nAC);
+      for (unsigned w = tid; w < n; w += kThreads) {
+        const int t = (int)fAC.div(w), r = (int)(w - (unsigned)t * nAC);
+        const int A = (int)fC.div(r), C = r - A * nC;
+        d.out[(long long)(pao.x + A) * d.ldD + __ldg(d.aux_ao + aux0 + t) + C] = sm[BUF_T(cur, A * nC + C, t)];
+      }
+      return;
+    }
     if (d.digest == 2) {
       // ---- gradient digestion: contract the derivative block with
       // W = w D_ab c_P (Cartesian in the bra) without storing it.

@@ -2,6 +2,7 @@
 // (eri3c.cu).  Not part of the public C ABI.
 #pragma once
 #include <cstdint>
+#include <cuda_runtime.h>
 #include <vector_types.h>
 #include <vector>
 #include <string>
@@ -110,6 +111,8 @@ struct ClassDesc {
   //   gamma[aux_ao[q] + C] += w * sum_AB I[A][B][C] D[ao_a + A][ao_b + B]
   //   J[ao_a + A][ao_b + B] += wj * sum_{q,C} I[A][B][C] c[aux_ao[q] + C]
   // w = 2 (1 for a == b), wj = 1 (1/2 for a == b); J is symmetrised afterwards.
+  // digest == 3 stores a block with nB = 1 into the matrix out with row stride
+  // ldD: out[(ao_a + A) * ldD + aux_ao[q] + C] (the 2-centre metric).
   int digest;
   int dscr;                // digestion scratch (doubles): D block [nA*nB], then c [T][nC]
   long long ldD;           // row stride of D and J
@@ -270,6 +273,9 @@ struct lx3c_basis {
 };
 
 namespace lx3c {
+// Allocate and fill the device copy of a basis from its host vectors
+// (synchronises st).  No validation: callers check the shell table first.
+int basis_upload(lx3c_basis* b, cudaStream_t st);
 void split_orientation(const lx3c_basis* orb, int a, int b, int la, int lb, std::vector<int>& primA,
                        std::vector<int>& primB);
 }  // namespace lx3c
