@@ -237,12 +237,14 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  *   flags bit 0: also prepare the nuclear gradient (lx3c_dfj_grad); needs an
  *   atom index on every shell and orbital shells with l < LX3C_LMAX_ORB.
  *   Screening: a (pair, ket) triple is kept when Q_ab Q_P >= schwarz_tol, with
- *   Q_ab = sum over primitive pairs of |c_a c_b| exp(-za zb/g AB^2)
+ *   Q_ab = 20 sum over primitive pairs of |c_a c_b| exp(-za zb/g AB^2)
  *   sqrt(2 pi^{5/2}/(g^2 sqrt(2g))) (|PA|^2+1/(2g))^{la/2} (|PB|^2+1/(2g))^{lb/2}
- *   and Q_P = sum |c_c| sqrt(2 pi^{5/2}/(z^2 sqrt(2z))) (1/(2z))^{lc/2}, an
- *   estimate of sqrt(max|(ab|ab)|) and sqrt(max|(P|P)|) -- an estimate, not a
- *   strict bound: dropped triples can hold integrals up to ~10x the tolerance.
- *   Pass 0 to keep all.
+ *   and Q_P = sum |c_c| sqrt(2 pi^{5/2}/(z^2 sqrt(2z))) (1/(2z))^{lc/2}: 20x an
+ *   analytic estimate of sqrt(max|(ab|ab)|) sqrt(max|(P|P)|), which is not a
+ *   bound by itself (the largest element of a triple reaches ~11x the
+ *   unscaled estimate on the DF-J recipe's clusters); the factor 20 keeps the
+ *   dropped integrals below schwarz_tol there (lx3c_schwarz_pair/aux return
+ *   the library's Q values).  Pass 0 to keep all.
  *   Returns LX3C_ENOTSUP for orbital shells above LX3C_LMAX_ORB.
  * lx3c_dfj_execute: D (device, nao x nao row-major, symmetric), c (device,
  *   naux_ao) in; gamma (device, naux_ao) and J (device, nao x nao, symmetric)
@@ -270,6 +272,13 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  */
 lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basis* aux, double schwarz_tol,
                           int flags, void* stream);
+/* The screening factors Q_ab (with the factor 20) and Q_P of lx3c_dfj_plan for
+ * one shell pair (l, K, centre[3], exponents[K], coefficients[K] per shell)
+ * or one ket shell; host only, no device needed.  LX3C_EINVAL on NULL or
+ * l < 0, K < 1. */
+lx3c_status lx3c_schwarz_pair(int la, int ka, const double* A, const double* ea, const double* ca, int lb, int kb,
+                              const double* B, const double* eb, const double* cb, double* q);
+lx3c_status lx3c_schwarz_aux(int l, int k, const double* e, const double* c, double* q);
 lx3c_status lx3c_dfj_execute(lx3c_dfj* plan, const double* D, const double* c, double* gamma, double* J,
                              void* stream);
 lx3c_status lx3c_dfj_energy(lx3c_dfj* plan, const double* D, const double* c, double* gamma, double* energy,

@@ -466,6 +466,29 @@ def fp64_rate(iters=1 << 16, stream=None):
     return g.value, ms.value
 
 
+def schwarz_factors(orb, pairs, aux, kets):
+    """The DF-J plan's screening factors (host only): Q_ab for each pair of
+    orb shells and Q_P for each ket shell (lx3c_schwarz_pair / lx3c_schwarz_aux);
+    a triple is kept when Q_ab Q_P >= tol."""
+    L = _lib.load()
+    f = lambda b, s: (int(b.l[s]), int(b.k[s]), np.ascontiguousarray(b.xyz[s], np.float64),
+                      np.ascontiguousarray(b.exps[b.off[s]:b.off[s] + b.k[s]], np.float64),
+                      np.ascontiguousarray(b.coefs[b.off[s]:b.off[s] + b.k[s]], np.float64))
+    qp, qa = np.zeros(len(pairs)), np.zeros(len(kets))
+    q = ctypes.c_double()
+    for i, (a, b) in enumerate(pairs):
+        la, ka, A, ea, ca = f(orb, a)
+        lb, kb, B, eb, cb = f(orb, b)
+        check(L.lx3c_schwarz_pair(la, ka, ptr(A), ptr(ea), ptr(ca), lb, kb, ptr(B), ptr(eb), ptr(cb),
+                                  ctypes.byref(q)), "lx3c_schwarz_pair")
+        qp[i] = q.value
+    for i, s in enumerate(kets):
+        l, k, _, e, c = f(aux, s)
+        check(L.lx3c_schwarz_aux(l, k, ptr(e), ptr(c), ctypes.byref(q)), "lx3c_schwarz_aux")
+        qa[i] = q.value
+    return qp, qa
+
+
 def class_flops(la, lb, lc, Kab, Kc=1, bra_pure=True):
     f = ctypes.c_double()
     check(_lib.load().lx3c_class_flops(la, lb, lc, Kab, Kc, int(bool(bra_pure)), ctypes.byref(f)), "lx3c_class_flops")

@@ -45,6 +45,9 @@ EXPORTS = {
                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lx3c_dfj_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    "lx3c_schwarz_pair": (ctypes.c_int, [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 3 +
+                          [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 3 + [c_f64p]),
+    "lx3c_schwarz_aux": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, c_f64p]),
     "lx3c_dfj_grad": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "lx3c_dfj_energy": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "lx3c_dfj_execute": (ctypes.c_int, [ctypes.c_void_p] * 6),

@@ -107,37 +107,47 @@ constexpr double kPi = 3.14159265358979323846;
 // sqrt of a Schwarz-type estimate of max |(ab|ab)| for a shell pair: the
 // (ss|ss) value of each primitive pair times the rms size of (x-A)^la (x-B)^lb
 // under the product Gaussian.
-double q_pair(const lx3c_basis* b, int sa, int sb) {
-  const double* A = &b->xyz[3 * sa];
-  const double* B = &b->xyz[3 * sb];
+double q_pair_raw(int la, int ka, const double* A, const double* ea, const double* ca, int lb, int kb,
+                  const double* B, const double* eb, const double* cb) {
   double ab2 = 0;
   for (int x = 0; x < 3; ++x) ab2 += (A[x] - B[x]) * (A[x] - B[x]);
   double q = 0;
-  for (int ia = 0; ia < b->k[sa]; ++ia)
-    for (int ib = 0; ib < b->k[sb]; ++ib) {
-      const double za = b->exps[b->off[sa] + ia], zb = b->exps[b->off[sb] + ib], g = za + zb;
+  for (int ia = 0; ia < ka; ++ia)
+    for (int ib = 0; ib < kb; ++ib) {
+      const double za = ea[ia], zb = eb[ib], g = za + zb;
       double pa2 = 0, pb2 = 0;
       for (int x = 0; x < 3; ++x) {
         const double P = (za * A[x] + zb * B[x]) / g;
         pa2 += (P - A[x]) * (P - A[x]);
         pb2 += (P - B[x]) * (P - B[x]);
       }
-      q += std::fabs(b->coefs[b->off[sa] + ia] * b->coefs[b->off[sb] + ib]) * std::exp(-za * zb / g * ab2) *
-           std::sqrt(2.0 * std::pow(kPi, 2.5) / (g * g * std::sqrt(2.0 * g))) *
-           std::pow(pa2 + 0.5 / g, 0.5 * b->l[sa]) * std::pow(pb2 + 0.5 / g, 0.5 * b->l[sb]);
+      q += std::fabs(ca[ia] * cb[ib]) * std::exp(-za * zb / g * ab2) *
+           std::sqrt(2.0 * std::pow(kPi, 2.5) / (g * g * std::sqrt(2.0 * g))) * std::pow(pa2 + 0.5 / g, 0.5 * la) *
+           std::pow(pb2 + 0.5 / g, 0.5 * lb);
     }
   return q;
 }
 
-double q_aux(const lx3c_basis* b, int s) {
+double q_aux_raw(int l, int k, const double* e, const double* c) {
   double q = 0;
-  for (int i = 0; i < b->k[s]; ++i) {
-    const double z = b->exps[b->off[s] + i];
-    q += std::fabs(b->coefs[b->off[s] + i]) * std::sqrt(2.0 * std::pow(kPi, 2.5) / (z * z * std::sqrt(2.0 * z))) *
-         std::pow(0.5 / z, 0.5 * b->l[s]);
-  }
+  for (int i = 0; i < k; ++i)
+    q += std::fabs(c[i]) * std::sqrt(2.0 * std::pow(kPi, 2.5) / (e[i] * e[i] * std::sqrt(2.0 * e[i]))) *
+         std::pow(0.5 / e[i], 0.5 * l);
   return q;
 }
+
+double q_pair(const lx3c_basis* b, int sa, int sb) {
+  return q_pair_raw(b->l[sa], b->k[sa], &b->xyz[3 * sa], &b->exps[b->off[sa]], &b->coefs[b->off[sa]], b->l[sb],
+                    b->k[sb], &b->xyz[3 * sb], &b->exps[b->off[sb]], &b->coefs[b->off[sb]]);
+}
+
+double q_aux(const lx3c_basis* b, int s) { return q_aux_raw(b->l[s], b->k[s], &b->exps[b->off[s]], &b->coefs[b->off[s]]); }
+
+// The estimate Q_ab Q_P is not a bound: on jittered clusters of the DF-J
+// recipe the largest element of a triple reaches ~11x it (compact same-shell
+// pairs).  A triple is kept when kSchwarzSafety Q_ab Q_P >= tol, so that the
+// dropped triples stay below tol with that margin.
+constexpr double kSchwarzSafety = 20.0;
 
 struct DfjLaunch {
   ClassDesc desc;
@@ -313,7 +323,7 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
       const auto& kl = kk.second;
       for (auto& e : kl) g.auxs.push_back(e.second);
       for (size_t i = 0; i < pl.size(); ++i) {
-        const double thr = ql[i] > 0 ? schwarz_tol / ql[i] : 1e308;
+        const double thr = ql[i] > 0 ? schwarz_tol / (kSchwarzSafety * ql[i]) : 1e308;
         // number of ket shells with Q_P >= thr (prefix of the sorted list)
         int lo = 0, hi = (int)kl.size();
         while (lo < hi) {
@@ -590,6 +600,20 @@ lx3c_status lx3c_dfj_grad(lx3c_dfj* p, const double* D, const double* c, double*
       }
     }
   }
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_schwarz_pair(int la, int ka, const double* A, const double* ea, const double* ca, int lb, int kb,
+                              const double* B, const double* eb, const double* cb, double* q) {
+  if (!A || !ea || !ca || !B || !eb || !cb || !q || la < 0 || lb < 0 || ka < 1 || kb < 1)
+    return dfail(LX3C_EINVAL, "schwarz_pair: bad argument");
+  *q = kSchwarzSafety * q_pair_raw(la, ka, A, ea, ca, lb, kb, B, eb, cb);
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_schwarz_aux(int l, int k, const double* e, const double* c, double* q) {
+  if (!e || !c || !q || l < 0 || k < 1) return dfail(LX3C_EINVAL, "schwarz_aux: bad argument");
+  *q = q_aux_raw(l, k, e, c);
   return LX3C_OK;
 }
 

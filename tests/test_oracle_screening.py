@@ -1,61 +1,57 @@
-"""Quality of the DF-J screening estimate (the reading of "identical
-screening": keep (pair, ket) when Q_ab Q_P >= tol, with the analytic Q of
-lx3c_dfj_plan's header comment restated here).  The oracle evaluates every
-triple the estimate drops on a stretched 4-atom cluster of the 256-atom
-recipe's shells: the estimate is not a strict bound (it can fall ~11x below
-the largest element of a triple, worst for compact same-shell pairs), so at
-tol = 1e-12 the dropped integrals must stay below 2e-11."""
+"""The DF-J screen (the reading of "Schwarz screening at 1e-12"): a triple
+(pair, ket) is kept when Q_ab Q_P >= tol, with the library's own factors
+(lx3c_schwarz_pair / lx3c_schwarz_aux, host-only calls; Q_ab carries a
+safety factor of 20 over an analytic estimate of sqrt(max|(ab|ab)|)).
+
+The oracle evaluates every triple the screen drops, on clusters of the DF-J
+recipe (4s3p2d1f orbital, 10s7p5d3f2g1h aux): at tol = 1e-12 every dropped
+integral is at most tol, and the screen's effect on gamma and J -- the
+dropped triples' contributions, with D = C C^T and c ~ N(0, 1) -- is
+reported and bounded."""
 import numpy as np
+import pytest
 
 import oracle
+import paper_2210_03192_gb300 as lx
 from paper_2210_03192_gb300 import workloads as W
 
 TOL = 1e-12
 
 
-def q_pair(b, sa, sb):
-    A, B = b.xyz[sa], b.xyz[sb]
-    ab2 = float(((A - B) ** 2).sum())
-    q = 0.0
-    for i in range(b.k[sa]):
-        for j in range(b.k[sb]):
-            za, zb = b.exps[b.off[sa] + i], b.exps[b.off[sb] + j]
-            g = za + zb
-            P = (za * A + zb * B) / g
-            q += (abs(b.coefs[b.off[sa] + i] * b.coefs[b.off[sb] + j]) * np.exp(-za * zb / g * ab2)
-                  * np.sqrt(2 * np.pi ** 2.5 / (g * g * np.sqrt(2 * g)))
-                  * (((P - A) ** 2).sum() + 0.5 / g) ** (0.5 * b.l[sa])
-                  * (((P - B) ** 2).sum() + 0.5 / g) ** (0.5 * b.l[sb]))
-    return q
-
-
-def q_aux(b, s):
-    z = b.exps[b.off[s]:b.off[s] + b.k[s]]
-    c = b.coefs[b.off[s]:b.off[s] + b.k[s]]
-    return float(np.sum(np.abs(c) * np.sqrt(2 * np.pi ** 2.5 / (z * z * np.sqrt(2 * z))) * (0.5 / z) ** (0.5 * b.l[s])))
-
-
-def test_dropped_triples_are_small():
-    cl = W.cluster((4, 1, 1), W.ORB_RECIPE_DFJ, W.AUX_RECIPE_DFJ, seed=81, spacing=3.0)
+def split(cl):
     orb, aux = cl.orb, cl.aux
-    qa = np.array([q_aux(aux, s) for s in range(aux.nshell)])
-    pairs, kets, est, kept = [], [], [], 0
-    for a in range(orb.nshell):
-        for b in range(a, orb.nshell):
-            qp = q_pair(orb, a, b)
-            for s in range(aux.nshell):
-                if qp * qa[s] < TOL:
-                    pairs.append((a, b))
-                    kets.append(s)
-                    est.append(qp * qa[s])
-                else:
-                    kept += 1
-    assert kept > len(kets) > 1000  # the cluster exercises the screen both ways
-    blocks = oracle.eri3c_triples(orb, aux, pairs, kets)
+    pairs = [(a, b) for a in range(orb.nshell) for b in range(a, orb.nshell)]
+    qp, qa = lx.schwarz_factors(orb, pairs, aux, range(aux.nshell))
+    keep = qp[:, None] * qa[None, :] >= TOL
+    return pairs, qp, qa, keep
+
+
+@pytest.mark.parametrize("shape,spacing,seed", [((4, 1, 1), 3.0, 81), ((2, 2, 1), 1.8, 82), ((3, 1, 1), 4.5, 83)])
+def test_dropped_triples_are_below_tolerance(shape, spacing, seed):
+    cl = W.cluster(shape, W.ORB_RECIPE_DFJ, W.AUX_RECIPE_DFJ, seed=seed, spacing=spacing)
+    pairs, qp, qa, keep = split(cl)
+    ip, iq = np.nonzero(~keep)
+    assert keep.sum() > len(ip) > 500  # the cluster exercises the screen both ways
+    blocks = oracle.eri3c_triples(cl.orb, cl.aux, [pairs[i] for i in ip], iq)
     big = np.array([np.abs(x).max() for x in blocks])
-    assert big.max() < 20 * TOL, big.max()
-    est = np.array(est)
-    ok = est > 0
-    ratio = big[ok] / est[ok]
-    assert ratio.max() < 20, ratio.max()
-    assert big[~ok].max(initial=0.0) == 0.0  # estimate underflowed to 0 only where the integrals do
+    assert big.max() <= TOL, big.max()
+    est = qp[ip] * qa[iq]
+    assert big[est == 0].max(initial=0.0) == 0.0  # the estimate underflows to 0 only where the integrals do
+
+
+def test_screening_error_in_gamma_and_J():
+    """Contributions of the dropped triples to gamma_P = sum (mu nu|P) D_mu nu
+    and J_mu nu = sum_P (mu nu|P) c_P on a 16-atom cluster of the recipe."""
+    cl = W.cluster((4, 2, 2), W.ORB_RECIPE_DFJ, W.AUX_RECIPE_DFJ, seed=W.SEED_BASE + 2)
+    pairs, qp, qa, keep = split(cl)
+    rng = np.random.default_rng(2)
+    n = int(oracle.ao_offsets(cl.orb)[-1])
+    D = W.density(rng, n)
+    c = rng.standard_normal(int(oracle.ao_offsets(cl.aux)[-1]))
+    ip, iq = np.nonzero(~keep)
+    tasks = np.stack([[pairs[i][0] for i in ip], [pairs[i][1] for i in ip], iq], axis=1)
+    dg, dJ = oracle.dfj(cl.orb, cl.aux, D, c, tasks=tasks)
+    # the dropped integrals are below 1e-12; weighted by D (|D| <~ n/5) and
+    # summed over the dropped pairs of a ket they stay far below gamma's scale
+    assert np.abs(dg).max() <= 1e-9, np.abs(dg).max()
+    assert np.abs(dJ).max() <= 1e-10, np.abs(dJ).max()
