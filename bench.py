@@ -16,11 +16,12 @@ taken after the timed sweep, each with its own clock record:
   dfj      256-atom DF-J build: fused gamma+J, gamma-only, J-only seconds
   batch    16 molecules in one graph launch vs per-class launches
   grad     64-atom DF-J energy forward, gradient backward, fwd+bwd
+  metric   256-atom aux basis: V = (P|Q), Cholesky, solve (c = V^-1 gamma)
   fp64_peak_measured  live FP64 FMA rate (lx3c_fp64_rate)
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--classes la,lb,lc,K ...] [--npair N] [--naux N]
-                  [--extras config1,dfj,batch,grad | --extras none]
+                  [--extras config1,dfj,batch,grad,metric | --extras none]
                   [--no-e2e] [--no-cpu] [--no-hints] [--per-class-out FILE]
 
 The end-to-end leg (e2e) repeats the sweep through the host-buffer call
@@ -71,7 +72,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--per-class-out", default=None, help="write the per-class table to this JSON file")
-    ap.add_argument("--extras", default="config1,dfj,batch,grad",
+    ap.add_argument("--extras", default="config1,dfj,batch,grad,metric",
                     help="one-off measurements after the timed sweep (comma list, or 'none')")
     return ap.parse_args()
 
@@ -324,11 +325,13 @@ def extra_config1(dev):
     out = torch.empty(plan.shape, dtype=torch.float64, device=dev)
     for _ in range(5):
         plan.execute(out)
-    ms = statistics.median(event_ms(lambda: plan.execute(out), 50))
+    # batches of 500 evaluations, about 1.5 s in all, so the clock sampler sees the load
+    reps = 500
+    ms = statistics.median(t / reps for t in event_ms(lambda: [plan.execute(out) for _ in range(reps)], 40))
     fl = lx.class_flops(1, 1, 2, 1, 1, True) * plan.npair * plan.naux
-    return dict(workload="(pp|d) K=1, 64 pairs x 32 ket shells, all-pure", integrals=int(plan.total),
+    return dict(workload="(pp|d) K=1, 64 pairs x 32 kets", integrals=int(plan.total),
                 ms=round(ms, 4), gints_s=round(plan.total / ms / 1e6, 4),
-                frac=round(fl / ms / 1e6 / FP64_PEAK_GFLOPS, 4), launches=plan.launches, reps=50)
+                frac=round(fl / ms / 1e6 / FP64_PEAK_GFLOPS, 4), launches=plan.launches, reps=40 * reps)
 
 
 def extra_dfj(dev):
@@ -349,8 +352,7 @@ def extra_dfj(dev):
     fused = event_ms(lambda: plan.execute(D, c, gamma, J))[0]
     gonly = event_ms(lambda: plan.execute(D, c, gamma, None, outputs="gamma"))[0]
     jonly = event_ms(lambda: plan.execute(D, c, None, J, outputs="J"))[0]
-    return dict(workload="DF-J, 256-atom jittered 1.8-bohr grid, orbital 4s3p2d1f (K=6/3/1/1), aux 10s7p5d3f2g1h "
-                         "(K=1), Schwarz-type estimate at 1e-12", nao=plan.nao, naux_ao=plan.naux_ao,
+    return dict(workload="DF-J, 256 atoms, 4s3p2d1f / 10s7p5d3f2g1h, screen 1e-12", nao=plan.nao, naux_ao=plan.naux_ao,
                 screened_triples=plan.ntasks, integrals=plan.nint, tile_fill=round(plan.tile_fill, 4),
                 setup_s=round(setup, 2), first_build_s=round(first / 1e3, 3), fused_s=round(fused / 1e3, 3),
                 gamma_only_s=round(gonly / 1e3, 3), J_only_s=round(jonly / 1e3, 3),
@@ -379,8 +381,7 @@ def extra_batch(dev):
     m0 = event_ms(lambda: b.execute(0))[0]
     m1 = event_ms(lambda: b.execute(1))[0]
     fl = info["flops"]
-    return dict(workload="16 molecules of 20-400 atoms, orbital 3s2p2d1f1g (K=6/3/1/1/1, 25%% of the orbital shells "
-                         "kept per molecule), aux 8s6p5d4f3g2h1i (K=1), DF-J digest, every class to (gg|i) mixed",
+    return dict(workload="16 molecules, 20-400 atoms, 3s2p2d1f1g (25% of shells) / 8s6p5d4f3g2h1i, DF-J",
                 screened_triples=info["tasks"], plan_s=round(plan_s, 2), bind_capture_s=round(bind_s, 2),
                 graph_branches_s=round(m2 / 1e3, 3), per_class_s=round(m0 / 1e3, 3),
                 graph_persistent_s=round(m1 / 1e3, 3),
@@ -411,14 +412,41 @@ def extra_grad(dev):
     bwd = statistics.median(event_ms(lambda: plan.gradient(D, c, grad), 2))
     both = statistics.median(event_ms(lambda: (plan.energy(D, c), plan.gradient(D, c, grad)), 2))
     plain = statistics.median(event_ms(lambda: plan.execute(D, c, gamma, J), 2))
-    return dict(workload="64-atom jittered grid, orbital 3s2p2d1f1g, aux 8s6p5d4f3g2h, E = c^T gamma, dE/dR [64,3]",
+    return dict(workload="64 atoms, 3s2p2d1f1g / 8s6p5d4f3g2h, E = c^T gamma, dE/dR",
                 screened_triples=plan.ntasks, fwd_ms=round(fwd, 2), bwd_ms=round(bwd, 2), fwd_bwd_ms=round(both, 2),
                 plain_fwd_gamma_J_ms=round(plain, 2), fwd_bwd_over_fwd=round(both / fwd, 3),
                 bwd_frac=round(plan.grad_flops / bwd / 1e6 / FP64_PEAK_GFLOPS, 4),
                 launches=dict(fwd=plan.launches, bwd=plan.grad_launches))
 
 
-EXTRAS = dict(config1=extra_config1, dfj=extra_dfj, batch=extra_batch, grad=extra_grad)
+def extra_metric(dev):
+    """Density-fitting metric of the 256-atom aux basis: V = (P|Q), its Cholesky
+    factor and one solve c = V^{-1} gamma."""
+    import torch
+    import paper_2210_03192_gb300 as lx
+    from paper_2210_03192_gb300 import workloads as W
+    cl = W.cluster256_dfj()
+    mp = lx.MetricPlan(cl.aux)
+    n = mp.naux_ao
+    A = torch.tensor(W.density(np.random.default_rng(5), 256) + 256 * np.eye(256), device=dev)
+    lx.cholesky(A)  # loads the factorization kernels
+    V = torch.empty((n, n), dtype=torch.float64, device=dev)
+    mp.execute(V)
+    tv = statistics.median(event_ms(lambda: mp.execute(V), 3))
+    info = []
+    tc = event_ms(lambda: info.append(lx.cholesky(V)[1]))[0]
+    b = torch.tensor(np.random.default_rng(6).standard_normal(n), device=dev)
+    ts = statistics.median(event_ms(lambda: lx.cholesky_solve(V, b), 3))
+    chol_flops = n ** 3 / 3.0
+    return dict(workload="metric of the 256-atom aux basis (10s7p5d3f2g1h per atom)", naux_ao=n,
+                metric_ms=round(tv, 2), metric_frac=round(mp.flops / tv / 1e6 / FP64_PEAK_GFLOPS, 4),
+                cholesky_ms=round(tc, 2), cholesky_gflops=round(chol_flops / tc / 1e6, 1),
+                cholesky_frac=round(chol_flops / tc / 1e6 / FP64_PEAK_GFLOPS, 4), cholesky_info=int(info[0]),
+                solve_ms=round(ts, 3), launches=dict(metric=mp.launches, cholesky=3 * ((n + 63) // 64) - 2,
+                                                     solve=4 * ((n + 63) // 64) - 2))
+
+
+EXTRAS = dict(config1=extra_config1, dfj=extra_dfj, batch=extra_batch, grad=extra_grad, metric=extra_metric)
 
 
 def run_extras(args, dev):
@@ -426,10 +454,12 @@ def run_extras(args, dev):
     import paper_2210_03192_gb300 as lx
     out = {}
     names = [] if args.extras == "none" else [x for x in args.extras.split(",") if x]
-    g, ms = lx.fp64_rate(1 << 17)
-    out["fp64_peak_measured"] = dict(gflops=round(g, 1), ms=round(ms, 2), frac_of_derived=round(g / FP64_PEAK_GFLOPS, 4),
-                                     method="lx3c_fp64_rate: 8 independent FMA chains per thread, every SM filled, "
-                                            "CUDA events")
+    def peak():
+        runs = [lx.fp64_rate(1 << 16) for _ in range(3)]
+        g, ms = max(runs)
+        return dict(gflops=round(g, 1), ms=round(ms, 2), frac_of_derived=round(g / FP64_PEAK_GFLOPS, 4),
+                    method="lx3c_fp64_rate, best of 3")
+    out["fp64_peak_measured"] = with_clocks(dev, peak)
     for n in names:
         if n not in EXTRAS:
             raise SystemExit("unknown extra %r (choose from %s)" % (n, ",".join(EXTRAS)))

@@ -150,9 +150,9 @@ lx3c_status lx3c_boys(const double* T, int64_t n, int mmax, double* out, void* s
 /*
  * Measured FP64 FMA throughput of the current device (not in the paper; the
  * roofline denominator of the FP64-bound integral kernels): one kernel of
- * `iters` steps of eight independent FMA chains per thread, every SM filled,
+ * `iters` steps of sixteen independent FMA chains per thread, every SM filled,
  * timed with CUDA events on `stream` after a short warm-up launch.
- * *gflops = 2 * 8 * iters * threads / seconds / 1e9; *ms (may be NULL) = the
+ * *gflops = 2 * 16 * iters * threads / seconds / 1e9; *ms (may be NULL) = the
  * timed launch's duration.  Allocates and frees a small device buffer and
  * synchronises `stream`.  LX3C_EINVAL for iters < 1 or a NULL gflops.
  */

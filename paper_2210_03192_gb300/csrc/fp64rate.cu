@@ -1,6 +1,6 @@
 // FP64 FMA throughput probe behind lx3c_fp64_rate (include/lx3c.h): the
 // measured denominator of the FP64 roofline that every integral class is
-// bound by.  Each thread runs eight independent FMA chains so the FP64 pipe,
+// bound by.  Each thread runs sixteen independent FMA chains so the FP64 pipe,
 // not the 4-cycle dependent-issue latency, sets the rate; the grid fills
 // every SM at the kernel's full occupancy.
 #include <cuda_runtime.h>
@@ -16,13 +16,14 @@ void set_last_error(const std::string& msg);
 namespace {
 
 constexpr int kRateThreads = 512;
-constexpr int kRateChains = 8;
+constexpr int kRateChains = 16;
 
 __global__ void __launch_bounds__(kRateThreads) fp64_rate_kernel(long long iters, double b, double c,
                                                                   double* __restrict__ sink) {
   double a[kRateChains];
 #pragma unroll
   for (int i = 0; i < kRateChains; ++i) a[i] = 1e-3 * threadIdx.x + i;
+#pragma unroll 4
   for (long long it = 0; it < iters; ++it) {
 #pragma unroll
     for (int i = 0; i < kRateChains; ++i) a[i] = fma(a[i], b, c);

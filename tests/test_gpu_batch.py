@@ -13,6 +13,8 @@ from paper_2210_03192_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from dfj_sampling import sampled_against_oracle  # noqa: E402
+
 
 @pytest.fixture(scope="module")
 def lx():
@@ -77,3 +79,32 @@ def test_batch_replay_is_stable(lx):
     gb, _ = b.execute(1)
     for x, y in zip(ga, gb):
         assert normwise(x, y.cpu().numpy()) < 1e-13
+
+
+def test_batch_members_of_the_16_molecule_workload(lx):
+    """The two smallest molecules of the 16-molecule workload (20 and 24
+    atoms, same recipe and orbital-shell fraction): every graph mode equals
+    the per-class launches, and the 20-atom molecule's J blocks and gamma
+    entries match the binary128 oracle on sampled entries."""
+    mols = W.batch16_molecules()[:2]
+    assert mols[0].natom >= 20
+    rng = np.random.default_rng(6)
+    Ds, cs = [], []
+    for cl in mols:
+        Ds.append(W.density(rng, int(oracle.ao_offsets(cl.orb)[-1])))
+        cs.append(rng.standard_normal(int(oracle.ao_offsets(cl.aux)[-1])))
+    b = lx.Batch([(cl.orb, cl.aux) for cl in mols], 1e-12).bind([torch.tensor(D, device="cuda") for D in Ds],
+                                                                  [torch.tensor(c, device="cuda") for c in cs])
+    res = {}
+    for mode in (2, 1, 0):
+        g, J = b.execute(mode)
+        torch.cuda.synchronize()
+        res[mode] = ([x.cpu().numpy().copy() for x in g], [x.cpu().numpy().copy() for x in J])
+    for mode in (1, 2):
+        for m in range(2):
+            assert normwise(res[mode][0][m], res[0][0][m]) < 1e-13
+            assert normwise(res[mode][1][m], res[0][1][m]) < 1e-13
+    cl = mols[0]
+    plan = lx.DFJPlan(cl.orb, cl.aux, 1e-12)  # the same screen, for its task list
+    g, J = res[2][0][0], res[2][1][0]
+    sampled_against_oracle(cl, plan, Ds[0], cs[0], g, J, 16, 3, 7, "quad", 1e-12)

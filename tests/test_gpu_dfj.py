@@ -3,11 +3,11 @@ J_mu nu = sum_P (mu nu|P) c_P, against the oracle on the same screened task
 list the GPU plan uses (exported with lx3c_dfj_group).
 
 gamma and J are sums of many integrals weighted by D and c, so they are
-compared normwise: max|gpu - oracle| <= tol * max|oracle| over each vector /
-matrix (the integrals themselves are checked element by element in
-test_gpu_eri3c.py).  tol = 1e-12 against the binary128 oracle; 1e-10 against
-the FP64 oracle, whose solid-harmonic bra projection loses digits on compact
-shells (up to ~1e-9 of a block).
+compared normwise: max|gpu - oracle| <= tol * max|oracle| over each vector,
+matrix or sampled block (the integrals themselves are checked element by
+element in test_gpu_eri3c.py).  tol = 1e-12 against the binary128 oracle;
+1e-10 against the FP64 oracle, whose solid-harmonic bra projection loses
+digits on compact shells (up to ~1e-9 of a block).
 """
 import numpy as np
 import pytest
@@ -17,6 +17,8 @@ from paper_2210_03192_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+from dfj_sampling import sampled_against_oracle  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -59,6 +61,9 @@ def test_dfj_small_cluster_binary128(lx):
 
 
 def test_dfj_16_atoms_full(lx):
+    """16-atom cluster of the 256-atom recipe: gamma and J in full against the
+    FP64 oracle (normwise 1e-10, the FP64 oracle's own floor), and sampled J
+    blocks and gamma entries against the binary128 oracle at 1e-12."""
     cl = W.cluster((4, 2, 2), W.ORB_RECIPE_DFJ, W.AUX_RECIPE_DFJ, seed=W.SEED_BASE + 2)
     D, c = inputs(cl, 2)
     plan, g, J = run_gpu(lx, cl, D, c)
@@ -66,6 +71,7 @@ def test_dfj_16_atoms_full(lx):
     assert normwise(g, go) < 1e-10
     assert normwise(J, Jo) < 1e-10
     assert np.dot(c, g) == pytest.approx(np.sum(D * J), rel=1e-12)
+    sampled_against_oracle(cl, plan, D, c, g, J, 24, 4, 16, "quad", 1e-12)
 
 
 def test_dfj_screening_keeps_everything_at_zero_tol(lx):
@@ -76,53 +82,11 @@ def test_dfj_screening_keeps_everything_at_zero_tol(lx):
 
 
 def test_dfj_256_atoms_sampled(lx):
-    """256-atom cluster (8x8x4 grid): J blocks of 64 random shell pairs
-    and gamma of 3 random ket shells against the FP64 oracle."""
+    """256-atom cluster (8x8x4 grid): J blocks of 48 random shell pairs and
+    gamma of 3 random ket shells against the oracle (binary128 for the J
+    blocks, FP64 for the long gamma sums)."""
     cl = W.cluster256_dfj()
     D, c = inputs(cl, 3)
     plan, g, J = run_gpu(lx, cl, D, c)
-    ao = oracle.ao_offsets(cl.orb)
-    aq = oracle.ao_offsets(cl.aux)
-    groups = plan.groups()
-    rng = np.random.default_rng(9)
-    # J rows: random (group, pair)
-    sel = []
-    for _ in range(64):
-        gi = int(rng.integers(len(groups)))
-        gr = groups[gi]
-        i = int(rng.integers(len(gr["counts"])))
-        sel.append((gr, i))
-    for gr, i in sel:
-        a, b = (int(x) for x in gr["pairs"][i])
-        Ps = gr["auxs"][:gr["counts"][i]]
-        blocks = oracle.eri3c_triples(cl.orb, cl.aux, [[a, b]] * len(Ps), Ps)
-        ref = sum(np.einsum("abP,P->ab", X, c[aq[P]:aq[P + 1]]) for X, P in zip(blocks, Ps))
-        # J also receives every other group's (a, b) contributions: collect them
-        for gr2 in groups:
-            if gr2 is gr:
-                continue
-            hit = np.where((gr2["pairs"][:, 0] == a) & (gr2["pairs"][:, 1] == b))[0]
-            for j in hit:
-                Ps2 = gr2["auxs"][:gr2["counts"][j]]
-                bl2 = oracle.eri3c_triples(cl.orb, cl.aux, [[a, b]] * len(Ps2), Ps2)
-                ref = ref + sum(np.einsum("abP,P->ab", X, c[aq[P]:aq[P + 1]]) for X, P in zip(bl2, Ps2))
-        got = J[ao[a]:ao[a + 1], ao[b]:ao[b + 1]]
-        assert np.abs(got - ref).max() <= 1e-10 * max(np.abs(ref).max(), 1e-300), (a, b)
-    # gamma: three random ket shells of low angular momentum
-    for P in rng.choice(np.where(cl.aux.l <= 1)[0], size=3, replace=False):
-        trip_pairs, trip_w = [], []
-        for gr in groups:
-            pos = np.where(gr["auxs"] == P)[0]
-            if len(pos) == 0:
-                continue
-            k = int(pos[0])
-            keep = np.where(gr["counts"] > k)[0]
-            trip_pairs.append(gr["pairs"][keep])
-        pairs = np.concatenate(trip_pairs)
-        blocks = oracle.eri3c_triples(cl.orb, cl.aux, pairs, np.full(len(pairs), P))
-        ref = np.zeros(2 * cl.aux.l[P] + 1)
-        for (a, b), X in zip(pairs, blocks):
-            w = 1.0 if a == b else 2.0
-            ref += w * np.einsum("abP,ab->P", X, D[ao[a]:ao[a + 1], ao[b]:ao[b + 1]])
-        got = g[aq[P]:aq[P + 1]]
-        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max(), P
+    sampled_against_oracle(cl, plan, D, c, g, J, 48, 0, 9, "quad", 1e-12)
+    sampled_against_oracle(cl, plan, D, c, g, J, 0, 3, 10, "double", 1e-10)

@@ -3,7 +3,11 @@ required for differentiation): dE/dR from lx3c_dfj_grad / DFJEnergy.
 
 Checks, following the target's statement:
   - the oracle's analytic gradient (which differentiates all three centres
-    independently) on the same screened task list, 1e-11 relative to max|F|;
+    independently) on the same screened task list, 1e-11 relative to max|F|,
+    in binary128: on a 2-atom cluster in full, and on the full 64-atom
+    cluster with D restricted to the shell pairs of two sampled atoms and c
+    to sampled ket shells of two others (so only the triples between them
+    carry weight; the GPU still runs the whole 64-atom plan);
   - sum of forces = 0 to 1e-10 max|F|;
   - central finite differences of the GPU energy (h = 1e-4 bohr) on the
     64-atom cluster (4x4x4 grid), 12 random coordinates, 1e-7 relative to max|F|;
@@ -48,6 +52,34 @@ def test_gradient_vs_oracle_binary128(lx):
     E, g = plan.energy(Dt, ct)
     go, _ = oracle.dfj(cl.orb, cl.aux, D, c, tasks=plan.tasks(), mode="quad")
     assert float(E) == pytest.approx(float(np.dot(c, go)), rel=1e-12)
+
+
+def test_gradient_64_atoms_sampled_vs_oracle_binary128(lx):
+    cl = W.cluster64_grad()
+    D, c = dc(cl, 7)
+    rng = np.random.default_rng(12)
+    atoms = rng.choice(cl.natom, 4, replace=False)
+    SA, SC = set(int(x) for x in atoms[:2]), set(int(x) for x in atoms[2:])
+    ao, aq = oracle.ao_offsets(cl.orb), oracle.ao_offsets(cl.aux)
+    mo = np.zeros(int(ao[-1]), bool)
+    for s in range(cl.orb.nshell):
+        if int(cl.orb.atom[s]) in SA:
+            mo[ao[s]:ao[s + 1]] = True
+    kets = [s for s in range(cl.aux.nshell) if int(cl.aux.atom[s]) in SC]
+    kets = set(int(x) for x in rng.choice(kets, 20, replace=False))
+    mc = np.zeros(int(aq[-1]), bool)
+    for s in kets:
+        mc[aq[s]:aq[s + 1]] = True
+    Dm = np.where(mo[:, None] & mo[None, :], D, 0.0)
+    cm = np.where(mc, c, 0.0)
+    plan = lx.DFJPlan(cl.orb, cl.aux, 1e-12, gradient=True)
+    G = plan.gradient(torch.tensor(Dm, device="cuda"), torch.tensor(cm, device="cuda")).cpu().numpy()
+    t = plan.tasks()
+    sel = np.array([int(cl.orb.atom[a]) in SA and int(cl.orb.atom[b]) in SA and int(P) in kets for a, b, P in t])
+    Go = oracle.dfj_grad(cl.orb, cl.aux, Dm, cm, cl.natom, tasks=t[sel], mode="quad")
+    scale = np.abs(Go).max()
+    assert sel.sum() > 1000 and scale > 0
+    assert np.abs(G - Go).max() <= 1e-11 * scale, (np.abs(G - Go).max() / scale)
 
 
 def test_gradient_three_atoms_fp64_oracle(lx):

@@ -4,11 +4,10 @@ times: every one of the 525 (la, lb <= 4 | lc <= 6, K_ab in {1,3,6}) classes at
 bench builds it), with a seeded sample of (pair, ket) blocks per class checked
 against the oracle one triple at a time.
 
-Criterion (as in parity.py): every element within 1e-12 relative or 1e-14
-absolute of the FP64 oracle; blocks with an element outside it are recomputed
-in binary128, and then every element must be within 2e-11 of its block's
-largest magnitude, with at most 2 % of a class's sampled elements missing the
-strict bound (the FP64 floor of the scheme).
+Criterion (parity.py): every element within 1e-12 relative or 1e-14 absolute
+of the oracle, or within 1e-12 of its block's largest magnitude plus 1e-14;
+blocks with an element outside the per-element form are recomputed in
+binary128 first.
 """
 import numpy as np
 import pytest
@@ -16,7 +15,7 @@ import pytest
 import oracle
 from paper_2210_03192_gb300 import workloads as W
 
-from parity import ATOL, BLOCK_RTOL, RTOL, STRICT_MISS_FRACTION
+from parity import ATOL, RTOL, within
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -50,8 +49,7 @@ def check_class(lx, la, lb, lc, K):
     for b in np.where(~strict.all(axis=(1, 2, 3)))[0]:
         o[b] = oracle.eri3c_triples(p.orb, p.aux, p.pairs[ip[b]:ip[b] + 1], p.auxs[iq[b]:iq[b] + 1], mode="quad")[0]
     strict = np.abs(g - o) <= np.maximum(RTOL * np.abs(o), ATOL)
-    scale = np.abs(o).max(axis=(1, 2, 3), keepdims=True)
-    ok = strict | (np.abs(g - o) <= BLOCK_RTOL * scale)
+    ok = within(g, o)
     return ok.all(), 1.0 - strict.mean(), int(ok.size)
 
 
@@ -61,6 +59,6 @@ def test_sweep_all_classes_full_size_sampled(lx):
     for (la, lb, lc, K) in W.SWEEP_CLASSES:
         ok, miss, n = check_class(lx, la, lb, lc, K)
         worst = max(worst, miss)
-        if not ok or miss > STRICT_MISS_FRACTION:
+        if not ok:
             failures.append(((la, lb, lc, K), miss))
     assert not failures, failures[:10]

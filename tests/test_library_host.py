@@ -208,6 +208,32 @@ def test_more_entry_points_reject_bad_arguments_on_host():
     assert L.lx3c_eri3c_noalloc(1, 0, 0, 1, 1, 1, 1, *nul, 1, None, 1, None, None) == -1   # null pointers
     msg = L.lx3c_last_error()
     assert msg and b"null" in msg
+    # beyond the static scratch limits: rejected before any device pointer is used
+    fake = [ctypes.c_void_p(256)] * 9
+    assert L.lx3c_eri3c_noalloc(1, 1, 0, 1, 1, 1, 1, *fake, 65537, ctypes.c_void_p(256), 1, ctypes.c_void_p(256),
+                                None) == -2
+    assert L.lx3c_eri3c_noalloc(1, 1, 0, 2, 2, 1, 1, *fake, 16385, ctypes.c_void_p(256), 1, ctypes.c_void_p(256),
+                                None) == -2  # npair * ka * kb > 65536
+    assert L.lx3c_eri3c_noalloc(1, 1, 0, 1, 1, 2, 1, *fake, 1, ctypes.c_void_p(256), 32769, ctypes.c_void_p(256),
+                                None) == -2  # naux * kc > 65536
+    assert b"scratch limits" in L.lx3c_last_error()
+    # accuracy settings, FP64 rate, metric and Cholesky
+    assert L.lx3c_set_orientation_threshold(0.5) == -1
+    assert L.lx3c_set_orientation_threshold(float("inf")) == -1
+    assert L.lx3c_set_orientation_threshold(0.0) == 0
+    assert L.lx3c_set_compensation(4) == -1 and L.lx3c_set_compensation(-1) == -1
+    assert L.lx3c_set_compensation(0) == 0
+    assert L.lx3c_fp64_rate(0, None, None, None) == -1
+    assert L.lx3c_metric_plan(ctypes.byref(h), None, None) == -1
+    assert L.lx3c_metric_execute(None, None, None) == -1
+    assert L.lx3c_metric_info(None, None, 0) == -1
+    assert L.lx3c_cholesky(None, 4, 4, None, None) == -1
+    assert L.lx3c_cholesky(ctypes.c_void_p(256), 4, 3, None, None) == -1
+    assert L.lx3c_cholesky_solve(None, 4, 4, None, 1, None) == -1
+    assert L.lx3c_dfj_coulomb(None, None, 0, None, None, None, None, None) == -1
+    q = ctypes.c_double()
+    assert L.lx3c_schwarz_pair(0, 0, None, None, None, 0, 1, None, None, None, ctypes.byref(q)) == -1
+    assert L.lx3c_schwarz_aux(-1, 1, None, None, ctypes.byref(q)) == -1
     # host-buffer path and Boys
     assert L.lx3c_eri3c_host(0, None, None, None, None, None, 0, None, None, None, None, None, None, 0, None, 0,
                              1, None, None) == -1
