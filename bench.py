@@ -17,11 +17,12 @@ taken after the timed sweep, each with its own clock record:
   batch    16 molecules in one graph launch vs per-class launches
   grad     64-atom DF-J energy forward, gradient backward, fwd+bwd
   metric   256-atom aux basis: V = (P|Q), Cholesky, solve (c = V^-1 gamma)
+  dfj_multi  per-density DF-J time, one density vs eight at once (32 atoms)
   fp64_peak_measured  live FP64 FMA rate (lx3c_fp64_rate)
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--classes la,lb,lc,K ...] [--npair N] [--naux N]
-                  [--extras config1,dfj,batch,grad,metric | --extras none]
+                  [--extras config1,dfj,batch,grad,metric,dfj_multi | --extras none]
                   [--no-e2e] [--no-cpu] [--no-hints] [--per-class-out FILE]
 
 The end-to-end leg (e2e) repeats the sweep through the host-buffer call
@@ -72,7 +73,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--per-class-out", default=None, help="write the per-class table to this JSON file")
-    ap.add_argument("--extras", default="config1,dfj,batch,grad,metric",
+    ap.add_argument("--extras", default="config1,dfj,batch,grad,metric,dfj_multi",
                     help="one-off measurements after the timed sweep (comma list, or 'none')")
     return ap.parse_args()
 
@@ -419,6 +420,28 @@ def extra_grad(dev):
                 launches=dict(fwd=plan.launches, bwd=plan.grad_launches))
 
 
+def extra_dfj_multi(dev):
+    """Per-density DF-J time with one density and with eight at once
+    (lx3c_dfj_execute_multi), 32-atom cluster of the 256-atom recipe."""
+    import torch
+    import paper_2210_03192_gb300 as lx
+    from paper_2210_03192_gb300 import workloads as W
+    cl = W.cluster((4, 4, 2), W.ORB_RECIPE_DFJ, W.AUX_RECIPE_DFJ, W.SEED_BASE + 2)
+    rng = np.random.default_rng(W.SEED_BASE + 5)
+    plan = lx.DFJPlan(cl.orb, cl.aux, 1e-12)
+    D8 = torch.tensor(np.stack([W.density(rng, plan.nao) for _ in range(8)]), device=dev)
+    c8 = torch.tensor(rng.standard_normal((8, plan.naux_ao)), device=dev)
+    gamma = torch.empty(plan.naux_ao, dtype=torch.float64, device=dev)
+    J = torch.empty((plan.nao, plan.nao), dtype=torch.float64, device=dev)
+    plan.execute(D8[0], c8[0], gamma, J)
+    plan.execute_multi(D8, c8)
+    t1 = statistics.median(event_ms(lambda: plan.execute(D8[0], c8[0], gamma, J), 3))
+    t8 = statistics.median(event_ms(lambda: plan.execute_multi(D8, c8), 3))
+    return dict(workload="DF-J, 32 atoms of the 256-atom recipe, gamma+J", screened_triples=plan.ntasks,
+                nd1_ms=round(t1, 2), nd8_ms=round(t8, 2), per_density_ms_nd8=round(t8 / 8, 2),
+                per_density_speedup=round(t1 / (t8 / 8), 3), digest="nd=8: mma.sync m8n8k4 f64 tiles")
+
+
 def extra_metric(dev):
     """Density-fitting metric of the 256-atom aux basis: V = (P|Q), its Cholesky
     factor and one solve c = V^{-1} gamma."""
@@ -446,7 +469,8 @@ def extra_metric(dev):
                                                      solve=4 * ((n + 63) // 64) - 2))
 
 
-EXTRAS = dict(config1=extra_config1, dfj=extra_dfj, batch=extra_batch, grad=extra_grad, metric=extra_metric)
+EXTRAS = dict(config1=extra_config1, dfj=extra_dfj, batch=extra_batch, grad=extra_grad, metric=extra_metric,
+              dfj_multi=extra_dfj_multi)
 
 
 def run_extras(args, dev):

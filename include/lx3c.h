@@ -251,6 +251,15 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  *   overwritten; either output may be NULL to skip it (not both).
  *   Asynchronous on `stream`.  Summation order inside gamma and J follows FP64
  *   atomic arrival order.
+ * lx3c_dfj_execute_multi: the same build for nd (1..8) densities and
+ *   coefficient vectors at once, sharing every integral: D (device, nd x nao
+ *   x nao), c (device, nd x naux_ao) in; gamma (nd x naux_ao) and J (nd x nao
+ *   x nao) overwritten, either may be NULL to skip it (then its input may be
+ *   NULL too).  Per tile the digestion is two small GEMMs (gamma: (tile kets x
+ *   components) x (pair block) times (pair block) x nd; J: (pair block) x
+ *   (tile kets x components) times that x nd) on FP64 tensor-core tiles
+ *   (mma.sync m8n8k4), nd zero-padded to 8.  LX3C_ENOTSUP if a class's
+ *   scratch does not fit.  Asynchronous.
  * lx3c_dfj_energy: gamma as above (J skipped) and *energy = c^T gamma
  *   (device scalar), the DF-J energy whose gradient lx3c_dfj_grad returns.
  * lx3c_dfj_info: out[0..10] = groups, screened (pair, ket shell) triples,
@@ -281,6 +290,8 @@ lx3c_status lx3c_schwarz_pair(int la, int ka, const double* A, const double* ea,
 lx3c_status lx3c_schwarz_aux(int l, int k, const double* e, const double* c, double* q);
 lx3c_status lx3c_dfj_execute(lx3c_dfj* plan, const double* D, const double* c, double* gamma, double* J,
                              void* stream);
+lx3c_status lx3c_dfj_execute_multi(lx3c_dfj* plan, int nd, const double* D, const double* c, double* gamma,
+                                   double* J, void* stream);
 lx3c_status lx3c_dfj_energy(lx3c_dfj* plan, const double* D, const double* c, double* gamma, double* energy,
                             void* stream);
 lx3c_status lx3c_dfj_grad(lx3c_dfj* plan, const double* D, const double* c, double* grad, void* stream);

@@ -203,6 +203,25 @@ class DFJPlan:
               "lx3c_dfj_execute")
         return gamma, J
 
+    def execute_multi(self, Ds, cs, outputs="both", stream=None):
+        """gamma [nd, naux_ao] and J [nd, nao, nao] for nd <= 8 densities Ds
+        [nd, nao, nao] and coefficient vectors cs [nd, naux_ao] at once
+        (lx3c_dfj_execute_multi); outputs="gamma" or "J" skips the other."""
+        torch = _torch()
+        nd = Ds.shape[0] if Ds is not None else cs.shape[0]
+        for name, t, n in (("Ds", Ds, nd * self.nao * self.nao), ("cs", cs, nd * self.naux_ao)):
+            if t is None:
+                continue
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise LibraryError("DFJPlan.execute_multi: %s must be a contiguous float64 CUDA tensor of %d" % (name, n))
+        dev = (Ds if Ds is not None else cs).device
+        gamma = None if outputs == "J" else torch.empty((nd, self.naux_ao), dtype=torch.float64, device=dev)
+        J = None if outputs == "gamma" else torch.empty((nd, self.nao, self.nao), dtype=torch.float64, device=dev)
+        vp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        check(_lib.load().lx3c_dfj_execute_multi(self.handle, int(nd), vp(Ds), vp(cs), vp(gamma), vp(J),
+                                                 _stream_handle(stream)), "lx3c_dfj_execute_multi")
+        return gamma, J
+
     def coulomb(self, L, D, stream=None):
         """DF-J Coulomb build with the metric's Cholesky factor L:
         gamma, c = V^{-1} gamma and J (lx3c_dfj_coulomb)."""

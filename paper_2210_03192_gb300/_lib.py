@@ -51,6 +51,7 @@ EXPORTS = {
     "lx3c_dfj_grad": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "lx3c_dfj_energy": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "lx3c_dfj_execute": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "lx3c_dfj_execute_multi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
     "lx3c_dfj_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lx3c_dfj_group": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
     "lx3c_dfj_destroy": (None, [ctypes.c_void_p]),

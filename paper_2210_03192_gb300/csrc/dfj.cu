@@ -568,6 +568,55 @@ lx3c_status lx3c_dfj_execute(lx3c_dfj* p, const double* D, const double* c, doub
   return LX3C_OK;
 }
 
+lx3c_status lx3c_dfj_execute_multi(lx3c_dfj* p, int nd, const double* D, const double* c, double* gamma, double* J,
+                                   void* stream) {
+  if (!p) return dfail(LX3C_EINVAL, "null plan");
+  if (nd < 1 || nd > 8) return dfail(LX3C_EINVAL, "execute_multi: nd must be in 1..8");
+  if ((gamma && !D) || (J && !c) || (!gamma && !J)) return dfail(LX3C_EINVAL, "execute_multi: null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long dstride = p->nao * p->nao, cstride = p->naux_ao;
+  // check every launch's scratch before launching anything
+  std::vector<ClassDesc> descs;
+  std::vector<int> grids;
+  for (auto& g : p->groups)
+    for (auto& L : g.L) {
+      if (!L.ntiles) continue;
+      ClassDesc d = L.desc;
+      d.digest = 4;
+      d.nd = nd;
+      d.dstride = dstride;
+      d.cstride = cstride;
+      d.D = D;
+      d.cvec = c;
+      d.gamma = gamma;
+      d.J = J;
+      const long long kAB = ((long long)d.onA * d.onB + 3) & ~3LL, kR = ((long long)d.T * d.nC + 3) & ~3LL;
+      d.dscr = place_epilogue_scratch(d, 8 * (kAB + kR));
+      if ((long long)d.smem_doubles * 8 > 232448) return dfail(LX3C_ENOTSUP, "execute_multi: scratch does not fit");
+      descs.push_back(d);
+      grids.push_back(L.grid);
+    }
+  if (gamma) DCUDA(cudaMemsetAsync(gamma, 0, (size_t)nd * cstride * 8, st));
+  if (J) DCUDA(cudaMemsetAsync(J, 0, (size_t)nd * dstride * 8, st));
+  size_t li = 0;
+  for (auto& g : p->groups) {
+    const long long np = (long long)g.counts.size(), na = (long long)g.auxs.size();
+    DCUDA(launch_pair_precompute(p->orb->dev(), g.d_pairs, np, g.Ka, g.Kb, g.d_pairrec, g.d_pairab, st));
+    DCUDA(launch_aux_precompute(p->aux->dev(), g.d_auxs, na, g.Kc, g.d_auxrec, g.d_auxc, st));
+    for (auto& L : g.L) {
+      if (!L.ntiles) continue;
+      DCUDA(launch_eri3c(descs[li], grids[li], st));
+      ++li;
+    }
+  }
+  if (J) {
+    dim3 blk(32, 8), grd((unsigned)((p->nao + 31) / 32), (unsigned)((p->nao + 7) / 8));
+    for (int k = 0; k < nd; ++k) symmetrize<<<grd, blk, 0, st>>>(J + k * dstride, p->nao);
+    DCUDA(cudaGetLastError());
+  }
+  return LX3C_OK;
+}
+
 lx3c_status lx3c_dfj_energy(lx3c_dfj* p, const double* D, const double* c, double* gamma, double* energy,
                             void* stream) {
   if (!energy || !gamma) return dfail(LX3C_EINVAL, "null pointer");

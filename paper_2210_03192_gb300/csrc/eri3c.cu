@@ -85,6 +85,15 @@ struct Dot2 {
   __device__ __forceinline__ double value() const { return __dadd_rn(s, c); }
 };
 
+// One FP64 tensor-core step D = A B + C on an 8x8x4 tile, one warp
+// (mma.sync m8n8k4 .f64).  With g = lane / 4 and q = lane % 4 the lane holds
+// A[g][q], B[q][g] and the accumulator elements C[g][2q], C[g][2q+1].
+__device__ __forceinline__ void dmma_8x8x4(double a, double b, double& c0, double& c1) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};\n"
+               : "+d"(c0), "+d"(c1)
+               : "d"(a), "d"(b));
+}
+
 // pref * F_m(T) for m = hi down to lo, written to v[(m - lo) * stride].
 // F_hi and exp(-T) come from the interpolation table (T < 117) or the
 // asymptotic form (T >= 117, exp(-T) = 0); lower orders by the downward
@@ -271,7 +280,11 @@ __device__ __forceinline__ void seg_dot(int nout, int len, const Prod& prod, con
 }
 
 // One tile: (sub-pair, up to T ket shells) through every stage, ending in the
-// store, the DF-J digestion or the gradient digestion.
+// store, the DF-J digestion or the gradient digestion.  kMulti instantiates
+// the several-density digestion on tensor-core tiles (digest == 4) in a
+// kernel of its own, so that the other launches keep the lower register
+// count of the plain instantiation.
+template <bool kMulti>
 __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, double* sm) {
   const unsigned tid = threadIdx.x;
   const int T = d.T, G = d.G, mode = d.mode, lc = d.lc, Lab = d.Lab;
@@ -735,6 +748,74 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       }
       return;
     }
+    if (kMulti) {
+      // ---- DF-J digestion for nd <= 8 densities at once, as two small GEMMs
+      // on FP64 tensor-core tiles (m8n8k4), with M rows per warp tile:
+      //   gamma[d][t][C] = wg * sum_s I[t][s][C] Ds[s][d]    (M = tv*nC, K = nAB)
+      //   J[d][s]        = wj * sum_{t,C} I[t][s][C] Cs[t*nC+C][d]  (M = nAB, K = tv*nC)
+      const int4 pao = __ldg(d.pair_ao + pair);
+      const double wg = pao.z ? 1.0 : 2.0, wj = pao.z ? 0.5 : 1.0;
+      const int nA = d.onA, nB = d.onB, nC = d.nC, nAB = nA * nB, R = tv * nC, nd = d.nd;
+      const int kAB = (nAB + 3) & ~3, kR = (R + 3) & ~3;
+      double* Ds = sm + d.dscr;      // [kAB][8]
+      double* Cs = Ds + kAB * 8;     // [kR][8]
+      for (int i = tid; i < kAB * 8; i += kThreads) {
+        const int r = i >> 3, dd = i & 7;  // r: storage index of (A, B)
+        const int A = d.orient ? r % nA : r / nB, B = d.orient ? r / nA : r % nB;
+        Ds[i] = (d.gamma && r < nAB && dd < nd)
+                    ? __ldg(d.D + dd * d.dstride + (long long)(pao.x + A) * d.ldD + pao.y + B)
+                    : 0.0;
+      }
+      for (int i = tid; i < kR * 8; i += kThreads) {
+        const int r = i >> 3, dd = i & 7;
+        double v = 0.0;
+        if (d.J && r < R && dd < nd) {
+          const int t = r / nC, C = r - t * nC;
+          v = __ldg(d.cvec + dd * d.cstride + __ldg(d.aux_ao + aux0 + t) + C);
+        }
+        Cs[i] = v;
+      }
+      __syncthreads();
+      const Buf cb = cur;
+      const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, q = lane & 3;
+      constexpr int kWarps = kThreads / 32;
+      if (d.gamma) {
+        for (int m0 = warp * 8; m0 < R; m0 += kWarps * 8) {
+          const int m = m0 + g;
+          const int t = m / nC, C = m - t * nC;
+          double c0 = 0.0, c1 = 0.0;
+          for (int k0 = 0; k0 < kAB; k0 += 4) {
+            const int k = k0 + q;
+            const double a = (m < R && k < nAB) ? sm[BUF_T(cb, k * nC + C, t)] : 0.0;
+            dmma_8x8x4(a, Ds[(k0 + q) * 8 + g], c0, c1);
+          }
+          if (m < R) {
+            double* gm = d.gamma + __ldg(d.aux_ao + aux0 + t) + C;
+            if (2 * q < nd) atomicAdd(gm + (2 * q) * d.cstride, wg * c0);
+            if (2 * q + 1 < nd) atomicAdd(gm + (2 * q + 1) * d.cstride, wg * c1);
+          }
+        }
+      }
+      if (d.J) {
+        for (int m0 = warp * 8; m0 < nAB; m0 += kWarps * 8) {
+          const int m = m0 + g;  // storage index s of the block
+          double c0 = 0.0, c1 = 0.0;
+          for (int k0 = 0; k0 < kR; k0 += 4) {
+            const int k = k0 + q;
+            const int t = k / nC, C = k - t * nC;
+            const double a = (m < nAB && k < R) ? sm[BUF_T(cb, m * nC + C, t)] : 0.0;
+            dmma_8x8x4(a, Cs[(k0 + q) * 8 + g], c0, c1);
+          }
+          if (m < nAB) {
+            const int A = d.orient ? m % nA : m / nB, B = d.orient ? m / nA : m % nB;
+            double* Jm = d.J + (long long)(pao.x + A) * d.ldD + pao.y + B;
+            if (2 * q < nd) atomicAdd(Jm + (2 * q) * d.dstride, wj * c0);
+            if (2 * q + 1 < nd) atomicAdd(Jm + (2 * q + 1) * d.dstride, wj * c1);
+          }
+        }
+      }
+      return;
+    }
     if (d.digest) {
       // ---- DF-J digestion (Sec. 3): the block never leaves shared memory.
       // With s the block's (A, B) index in its storage order:
@@ -812,7 +893,13 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
 // One class launch: CTAs stride over the class's tiles.
 __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__ ClassDesc d) {
   extern __shared__ double sm[];
-  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body(d, tile, sm);
+  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body<false>(d, tile, sm);
+}
+
+// The same for DF-J launches digesting several densities (digest == 4).
+__global__ void __launch_bounds__(kThreads) eri3c_multi_kernel(const __grid_constant__ ClassDesc d) {
+  extern __shared__ double sm[];
+  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body<true>(d, tile, sm);
 }
 
 // Persistent form for mixed workloads: every CTA pulls (descriptor, tile)
@@ -844,7 +931,7 @@ __global__ void __launch_bounds__(kThreads) eri3c_persistent(const ClassDesc* __
       cur = wk.x;
       __syncthreads();
     }
-    tile_body(sd, wk.y, sm);
+    tile_body<false>(sd, wk.y, sm);
   }
 }
 
@@ -886,10 +973,15 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(eri3c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(eri3c_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  eri3c_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);
+  if (d.digest == 4)
+    eri3c_multi_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);
+  else
+    eri3c_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);
   return cudaGetLastError();
 }
 

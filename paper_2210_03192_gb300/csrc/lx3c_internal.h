@@ -115,6 +115,12 @@ struct ClassDesc {
   // ldD: out[(ao_a + A) * ldD + aux_ao[q] + C] (the 2-centre metric).
   int digest;
   int dscr;                // digestion scratch (doubles): D block [nA*nB], then c [T][nC]
+  // several densities (digest == 4): nd <= 8 of them, D, cvec, gamma and J
+  // holding nd matrices / vectors spaced dstride (D, J) and cstride (cvec,
+  // gamma) doubles apart; the scratch holds the D blocks [nAB padded to 4][8]
+  // and the tile's c values [tv*nC padded to 4][8] (zero-padded to 8 columns)
+  int nd;
+  long long dstride, cstride;
   long long ldD;           // row stride of D and J
   const double* D;
   const double* cvec;
