@@ -294,6 +294,33 @@ lx3c_status lx3c_dfj_execute_multi(lx3c_dfj* plan, int nd, const double* D, cons
                                    double* J, void* stream);
 lx3c_status lx3c_dfj_energy(lx3c_dfj* plan, const double* D, const double* c, double* gamma, double* energy,
                             void* stream);
+
+/*
+ * Tile-callback DF-J build (paper Sec. 3: the DF-J builder's end-user
+ * interface receives tiles of the density matrix and writes tiles of J
+ * through callables, assuming nothing about their layout or distribution).
+ * The orbital AOs are cut into consecutive blocks of whole shells of about
+ * tile_ao AOs each; a tile is (row block, column block).
+ *   get_D(user, row0, nrow, col0, ncol, dst, ld): fill the host buffer dst
+ *     (nrow x ncol, row stride ld) with D[row0.., col0..]; asked for the
+ *     tiles with row block <= column block only (D must be symmetric).
+ *   put_J(user, row0, nrow, col0, ncol, src, ld): take J[row0.., col0..]
+ *     from the host buffer src (valid during the call only); called for every
+ *     tile, row-block-major, after the build.  May be NULL (gamma only).
+ *   Either callable returns 0 on success; any other value stops the build
+ *   with LX3C_EINVAL.
+ *   c (host, naux_ao) in; gamma (host, naux_ao) out, may be NULL.
+ * Device copies of D and J and two page-locked staging tiles are allocated
+ * and freed inside the call, which synchronises `stream`.  The callables run
+ * on the calling thread.
+ */
+typedef int (*lx3c_tile_get_fn)(void* user, int64_t row0, int64_t nrow, int64_t col0, int64_t ncol, double* dst,
+                                int64_t ld);
+typedef int (*lx3c_tile_put_fn)(void* user, int64_t row0, int64_t nrow, int64_t col0, int64_t ncol,
+                                const double* src, int64_t ld);
+lx3c_status lx3c_dfj_execute_tiles(lx3c_dfj* plan, int64_t tile_ao, lx3c_tile_get_fn get_D,
+                                   lx3c_tile_put_fn put_J, void* user, const double* c, double* gamma,
+                                   void* stream);
 lx3c_status lx3c_dfj_grad(lx3c_dfj* plan, const double* D, const double* c, double* grad, void* stream);
 lx3c_status lx3c_dfj_info(const lx3c_dfj* plan, double* out, int n);
 lx3c_status lx3c_dfj_group(const lx3c_dfj* plan, int gi, int32_t* info, int32_t* pairs, int32_t* counts,

@@ -203,6 +203,44 @@ class DFJPlan:
               "lx3c_dfj_execute")
         return gamma, J
 
+    def execute_tiles(self, get_D, put_J, c, tile_ao=256, stream=None):
+        """Tile-callback build (lx3c_dfj_execute_tiles): get_D(row0, nrow, col0, ncol)
+        returns that tile of D (array-like [nrow, ncol]); put_J(row0, col0, tile)
+        receives each tile of J (None: skip J).  c is host [naux_ao]; returns gamma
+        (numpy)."""
+        L = _lib.load()
+        errors = []
+
+        def g(user, r0, nr, c0, nc, dst, ld):
+            try:
+                t = np.asarray(get_D(int(r0), int(nr), int(c0), int(nc)), np.float64)
+                out = np.ctypeslib.as_array(dst, shape=(int(nr) * int(ld),)).reshape(int(nr), int(ld))
+                out[:, :nc] = t
+                return 0
+            except Exception as e:  # reported through the status
+                errors.append(e)
+                return 1
+
+        def p(user, r0, nr, c0, nc, src, ld):
+            try:
+                a = np.ctypeslib.as_array(src, shape=(int(nr) * int(ld),)).reshape(int(nr), int(ld))[:, :nc]
+                put_J(int(r0), int(c0), a.copy())
+                return 0
+            except Exception as e:
+                errors.append(e)
+                return 1
+
+        gf = _lib.TILE_FN(g)
+        pf = _lib.TILE_FN(p) if put_J is not None else ctypes.cast(None, _lib.TILE_FN)
+        c = np.ascontiguousarray(c, np.float64)
+        gamma = np.empty(self.naux_ao)
+        rc = L.lx3c_dfj_execute_tiles(self.handle, int(tile_ao), gf, pf, None, ptr(c), ptr(gamma),
+                                      _stream_handle(stream))
+        if errors:
+            raise errors[0]
+        check(rc, "lx3c_dfj_execute_tiles")
+        return gamma
+
     def execute_multi(self, Ds, cs, outputs="both", stream=None):
         """gamma [nd, naux_ao] and J [nd, nao, nao] for nd <= 8 densities Ds
         [nd, nao, nao] and coefficient vectors cs [nd, naux_ao] at once

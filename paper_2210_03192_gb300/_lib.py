@@ -16,6 +16,9 @@ _lib = None
 
 c_i32p = ctypes.POINTER(ctypes.c_int32)
 c_f64p = ctypes.POINTER(ctypes.c_double)
+# int f(void* user, int64 row0, int64 nrow, int64 col0, int64 ncol, double* buf, int64 ld)
+TILE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                           ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_int64)
 
 EXPORTS = {
     # name: (restype, argtypes)
@@ -51,6 +54,8 @@ EXPORTS = {
     "lx3c_dfj_grad": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "lx3c_dfj_energy": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "lx3c_dfj_execute": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "lx3c_dfj_execute_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, TILE_FN, TILE_FN, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lx3c_dfj_execute_multi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
     "lx3c_dfj_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lx3c_dfj_group": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),

@@ -241,6 +241,10 @@ struct lx3c_dfj {
   std::vector<int> sph_off;
 };
 
+namespace lx3c {
+const lx3c_basis* dfj_orbital_basis(const lx3c_dfj* plan) { return plan->orb; }
+}  // namespace lx3c
+
 extern "C" {
 
 void lx3c_dfj_destroy(lx3c_dfj* p) {
