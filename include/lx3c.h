@@ -249,8 +249,11 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  * lx3c_dfj_execute: D (device, nao x nao row-major, symmetric), c (device,
  *   naux_ao) in; gamma (device, naux_ao) and J (device, nao x nao, symmetric)
  *   overwritten; either output may be NULL to skip it (not both).
- *   Asynchronous on `stream`.  Summation order inside gamma and J follows FP64
- *   atomic arrival order.
+ *   Asynchronous on `stream`.  gamma and J are summed exactly in 128-bit
+ *   fixed point (each contribution rounded to a multiple of 2^-72, every
+ *   partial sum below 2^55 in magnitude) and rounded once to FP64, so the
+ *   result does not depend on the order in which tiles finish: repeated
+ *   executes of a plan are bitwise equal.
  * lx3c_dfj_execute_multi: the same build for nd (1..8) densities and
  *   coefficient vectors at once, sharing every integral: D (device, nd x nao
  *   x nao), c (device, nd x naux_ao) in; gamma (nd x naux_ao) and J (nd x nao
@@ -258,8 +261,9 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  *   NULL too).  Per tile the digestion is two small GEMMs (gamma: (tile kets x
  *   components) x (pair block) times (pair block) x nd; J: (pair block) x
  *   (tile kets x components) times that x nd) on FP64 tensor-core tiles
- *   (mma.sync m8n8k4), nd zero-padded to 8.  LX3C_ENOTSUP if a class's
- *   scratch does not fit.  Asynchronous.
+ *   (mma.sync m8n8k4), nd zero-padded to 8; gamma and J are summed with
+ *   FP64 atomics here (order-dependent in the last bits).  LX3C_ENOTSUP if a
+ *   class's scratch does not fit.  Asynchronous.
  * lx3c_dfj_energy: gamma as above (J skipped) and *energy = c^T gamma
  *   (device scalar), the DF-J energy whose gradient lx3c_dfj_grad returns.
  * lx3c_dfj_info: out[0..10] = groups, screened (pair, ket shell) triples,
@@ -272,7 +276,8 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  *   d/dA (ab|P) = sum_prim [2 za (a+1 b|P) - a (a-1 b|P)] (same for B) are
  *   formed on the fly in Cartesian-bra classes and contracted with
  *   W = w D_ab c_P; dE/dC = -(dE/dA + dE/dB) (translational invariance).
- *   grad (device, natom x 3) overwritten; accumulated with FP64 atomics.
+ *   grad (device, natom x 3) overwritten; summed in the same exact fixed
+ *   point as gamma and J (bitwise reproducible).
  * lx3c_dfj_group: the screened task list of class group gi (for checks):
  *   info[8] = {la, lb, lc, ka, kb, kc, npair, nket}; pairs[2*npair] shell
  *   indices (a, b); counts[npair]: pair i is kept with the first counts[i]

@@ -9,8 +9,10 @@
 // (la lb | lc) class group keeps its ket shells sorted by Q_P so that the
 // ket shells surviving Q_ab Q_P >= tol for a pair form a prefix of the list;
 // tiles (sub-pair, ket range) are tabulated.  Execution runs the class kernel
-// in digest mode: gamma and J are accumulated with FP64 atomics from each
-// tile's block in shared memory; a final kernel symmetrises J.
+// in digest mode: gamma and J are accumulated from each tile's block in
+// shared memory into exact fixed-point accumulators (fixed128.cuh), so the
+// result does not depend on the order of the contributions; final kernels
+// convert them to FP64 and symmetrise J.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +29,7 @@
 #include <vector>
 
 #include "../../include/lx3c.h"
+#include "fixed128.cuh"
 #include "lx3c_internal.h"
 
 namespace lx3c {
@@ -86,6 +89,32 @@ __global__ void symmetrize(double* J, long long n) {
     J[i * n + j] = s;
     J[j * n + i] = s;
   }
+}
+
+// out[i] = value of the fixed-point accumulator acc[i] (gamma, gradient)
+__global__ void fix_finish(const unsigned long long* __restrict__ acc, long long n, double* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fix_decode(acc + 2 * i);
+}
+
+// J[i][j] = A[i][j] + A[j][i] from the accumulated unique-pair blocks A (the
+// digest adds each unique shell pair's block once, diagonal shell blocks
+// with half weight, so this is exact on the diagonal too)
+__global__ void fix_finish_J(const unsigned long long* __restrict__ acc, long long n, double* __restrict__ J) {
+  const long long i = blockIdx.y * (long long)blockDim.y + threadIdx.y;
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n && j < n) J[i * n + j] = fix_decode(acc + 2 * (i * n + j)) + fix_decode(acc + 2 * (j * n + i));
+}
+
+cudaError_t launch_fix_finish(const unsigned long long* acc, long long n, double* out, cudaStream_t st) {
+  fix_finish<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(acc, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fix_finish_J(const unsigned long long* acc, long long n, double* J, cudaStream_t st) {
+  dim3 blk(32, 8), grd((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8));
+  fix_finish_J<<<grd, blk, 0, st>>>(acc, n, J);
+  return cudaGetLastError();
 }
 
 // energy = sum_i c_i gamma_i (one block, fixed-order tree reduction)
@@ -239,6 +268,10 @@ struct lx3c_dfj {
   std::vector<DfjGroup> groups;
   double* d_sph = nullptr;          // solid-harmonic matrices for l = 0..7
   std::vector<int> sph_off;
+  // exact fixed-point accumulators (two words per element): gamma, J, gradient
+  unsigned long long* d_gacc = nullptr;
+  unsigned long long* d_Jacc = nullptr;
+  unsigned long long* d_facc = nullptr;
 };
 
 namespace lx3c {
@@ -264,6 +297,9 @@ void lx3c_dfj_destroy(lx3c_dfj* p) {
     cudaFree(g.d_pair_atoms); cudaFree(g.d_aux_atom);
   }
   cudaFree(p->d_sph);
+  cudaFree(p->d_gacc);
+  cudaFree(p->d_Jacc);
+  cudaFree(p->d_facc);
   delete p;
 }
 
@@ -539,6 +575,9 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
           L.desc.Tb = p->d_sph + p->sph_off[g.lb];
         }
   }
+  DCUDA(cudaMalloc(&p->d_gacc, (size_t)p->naux_ao * 16));
+  DCUDA(cudaMalloc(&p->d_Jacc, (size_t)p->nao * p->nao * 16));
+  if (want_grad) DCUDA(cudaMalloc(&p->d_facc, (size_t)p->natom * 3 * 16));
   DCUDA(cudaStreamSynchronize(st));
   *out = p.release();
   return LX3C_OK;
@@ -548,8 +587,8 @@ lx3c_status lx3c_dfj_execute(lx3c_dfj* p, const double* D, const double* c, doub
   if (!p) return dfail(LX3C_EINVAL, "null plan");
   if (!D || !c || (!gamma && !J)) return dfail(LX3C_EINVAL, "null pointer");
   cudaStream_t st = (cudaStream_t)stream;
-  if (gamma) DCUDA(cudaMemsetAsync(gamma, 0, p->naux_ao * 8, st));
-  if (J) DCUDA(cudaMemsetAsync(J, 0, p->nao * p->nao * 8, st));
+  if (gamma) DCUDA(cudaMemsetAsync(p->d_gacc, 0, p->naux_ao * 16, st));
+  if (J) DCUDA(cudaMemsetAsync(p->d_Jacc, 0, p->nao * p->nao * 16, st));
   for (auto& g : p->groups) {
     const long long np = (long long)g.counts.size(), na = (long long)g.auxs.size();
     DCUDA(launch_pair_precompute(p->orb->dev(), g.d_pairs, np, g.Ka, g.Kb, g.d_pairrec, g.d_pairab, st));
@@ -559,16 +598,13 @@ lx3c_status lx3c_dfj_execute(lx3c_dfj* p, const double* D, const double* c, doub
       ClassDesc d = L.desc;
       d.D = D;
       d.cvec = c;
-      d.gamma = gamma;
-      d.J = J;
+      d.gacc = gamma ? p->d_gacc : nullptr;
+      d.Jacc = J ? p->d_Jacc : nullptr;
       DCUDA(launch_eri3c(d, L.grid, st));
     }
   }
-  if (J) {
-    dim3 blk(32, 8), grd((unsigned)((p->nao + 31) / 32), (unsigned)((p->nao + 7) / 8));
-    symmetrize<<<grd, blk, 0, st>>>(J, p->nao);
-    DCUDA(cudaGetLastError());
-  }
+  if (gamma) DCUDA(launch_fix_finish(p->d_gacc, p->naux_ao, gamma, st));
+  if (J) DCUDA(launch_fix_finish_J(p->d_Jacc, p->nao, J, st));
   return LX3C_OK;
 }
 
@@ -636,7 +672,7 @@ lx3c_status lx3c_dfj_grad(lx3c_dfj* p, const double* D, const double* c, double*
   if (!p->gradient) return dfail(LX3C_EINVAL, "plan was built without gradient support (flags & 1)");
   if (!D || !c || !grad) return dfail(LX3C_EINVAL, "null pointer");
   cudaStream_t st = (cudaStream_t)stream;
-  DCUDA(cudaMemsetAsync(grad, 0, (size_t)p->natom * 3 * 8, st));
+  DCUDA(cudaMemsetAsync(p->d_facc, 0, (size_t)p->natom * 3 * 16, st));
   for (auto& g : p->groups) {
     const long long np = (long long)g.counts.size(), na = (long long)g.auxs.size();
     DCUDA(launch_aux_precompute(p->aux->dev(), g.d_auxs, na, g.Kc, g.d_auxrec, g.d_auxc, st));
@@ -648,11 +684,12 @@ lx3c_status lx3c_dfj_grad(lx3c_dfj* p, const double* D, const double* c, double*
         ClassDesc d = L.desc;
         d.D = D;
         d.cvec = c;
-        d.grad = grad;
+        d.facc = p->d_facc;
         DCUDA(launch_eri3c(d, L.grid, st));
       }
     }
   }
+  DCUDA(launch_fix_finish(p->d_facc, (long long)p->natom * 3, grad, st));
   return LX3C_OK;
 }
 
@@ -672,7 +709,7 @@ lx3c_status lx3c_schwarz_aux(int l, int k, const double* e, const double* c, dou
 
 lx3c_status lx3c_dfj_info(const lx3c_dfj* p, double* out, int n) {
   if (!p || (!out && n > 0)) return dfail(LX3C_EINVAL, "null pointer");
-  double tasks = 0, nint = 0, flops = 0, launches = 1, gflops = 0, glaunches = 0, slots = 0;
+  double tasks = 0, nint = 0, flops = 0, launches = 2, gflops = 0, glaunches = p->gradient ? 1 : 0, slots = 0;
   for (auto& g : p->groups) {
     for (auto& L : g.L) slots += (double)L.ntiles * L.desc.T;
     tasks += (double)g.ntasks;
@@ -809,8 +846,8 @@ cudaError_t capture_branches(lx3c_batch* b, const std::vector<ClassDesc>& descs,
     const int nmol = (int)b->mols.size();
     for (int m = 0; m < nmol; ++m) {
       lx3c_dfj* p = b->mols[m];
-      cudaMemsetAsync(b->gamma[m], 0, p->naux_ao * 8, cap);
-      cudaMemsetAsync(b->J[m], 0, p->nao * p->nao * 8, cap);
+      cudaMemsetAsync(p->d_gacc, 0, p->naux_ao * 16, cap);
+      cudaMemsetAsync(p->d_Jacc, 0, p->nao * p->nao * 16, cap);
       for (auto& g : p->groups) {
         launch_pair_precompute(p->orb->dev(), g.d_pairs, (long long)g.counts.size(), g.Ka, g.Kb, g.d_pairrec,
                                g.d_pairab, cap);
@@ -834,9 +871,9 @@ cudaError_t capture_branches(lx3c_batch* b, const std::vector<ClassDesc>& descs,
       cudaStreamWaitEvent(cap, join[i], 0);
     }
     for (int m = 0; m < nmol; ++m) {
-      dim3 blk(32, 8), grd((unsigned)((b->mols[m]->nao + 31) / 32), (unsigned)((b->mols[m]->nao + 7) / 8));
-      symmetrize<<<grd, blk, 0, cap>>>(b->J[m], b->mols[m]->nao);
-      ++kernels;
+      launch_fix_finish(b->mols[m]->d_gacc, b->mols[m]->naux_ao, b->gamma[m], cap);
+      launch_fix_finish_J(b->mols[m]->d_Jacc, b->mols[m]->nao, b->J[m], cap);
+      kernels += 2;
     }
     ce = cudaStreamEndCapture(cap, &b->graph2);
     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec2, b->graph2, 0);
@@ -918,8 +955,9 @@ lx3c_status lx3c_batch_plan(lx3c_batch** out, int nmol, const lx3c_basis* const*
     if (!tg) {
       long long mx = 0, mxa = 0;
       for (auto* p : b->mols) { mx = std::max(mx, p->nao); mxa = std::max(mxa, p->naux_ao); }
-      DCUDA(cudaMalloc(&tg, mxa * 8)); DCUDA(cudaMalloc(&tc, mxa * 8));
-      DCUDA(cudaMalloc(&tJ, mx * mx * 8)); DCUDA(cudaMalloc(&tD, mx * mx * 8));
+      DCUDA(cudaMalloc(&tg, mxa * 16)); DCUDA(cudaMalloc(&tc, mxa * 8));
+      DCUDA(cudaMalloc(&tJ, mx * mx * 16)); DCUDA(cudaMalloc(&tD, mx * mx * 8));
+      DCUDA(cudaMemset(tg, 0, mxa * 16)); DCUDA(cudaMemset(tJ, 0, mx * mx * 16));
       DCUDA(cudaMemset(tc, 0, mxa * 8)); DCUDA(cudaMemset(tD, 0, mx * mx * 8));
     }
     DCUDA(launch_pair_precompute(owner->orb->dev(), g.d_pairs, (long long)g.counts.size(), g.Ka, g.Kb, g.d_pairrec,
@@ -948,7 +986,8 @@ lx3c_status lx3c_batch_plan(lx3c_batch** out, int nmol, const lx3c_basis* const*
     for (int T : cands) {
       if (!retile(L, g, b->ds, T)) continue;
       ClassDesc d = L.desc;
-      d.D = tD; d.cvec = tc; d.gamma = tg; d.J = tJ;
+      d.D = tD; d.cvec = tc;
+      d.gacc = (unsigned long long*)tg; d.Jacc = (unsigned long long*)tJ;
       long long nt = 0;
       for (long long s2 = 0; s2 < nsub_t; ++s2) nt += (g.counts[L.sub[s2].x] + T - 1) / T;
       d.ntiles = nt;
@@ -1002,14 +1041,14 @@ lx3c_status lx3c_batch_bind(lx3c_batch* b, const double* const* D, const double*
   b->plain_launches = 0;
   for (int m = 0; m < nmol; ++m) {
     lx3c_dfj* p = b->mols[m];
-    b->plain_launches += 1;
+    b->plain_launches += 2;
     for (auto& g : p->groups) {
       b->plain_launches += 2;
       for (auto& L : g.L) {
         if (!L.ntiles) continue;
         ++b->plain_launches;
         ClassDesc d = L.desc;
-        d.D = D[m]; d.cvec = c[m]; d.gamma = gamma[m]; d.J = J[m];
+        d.D = D[m]; d.cvec = c[m]; d.gacc = p->d_gacc; d.Jacc = p->d_Jacc;
         double fl = 0;
         lx3c_class_flops(d.la, d.lb, d.lc, d.Kab, d.Kc, 1, &fl);
         order.push_back({fl * (double)d.T * (double)L.ntiles, (int)descs.size()});
@@ -1043,8 +1082,8 @@ lx3c_status lx3c_batch_bind(lx3c_batch* b, const double* const* D, const double*
   b->graph_kernels = 0;
   for (int m = 0; m < nmol; ++m) {
     lx3c_dfj* p = b->mols[m];
-    cudaMemsetAsync(gamma[m], 0, p->naux_ao * 8, cap);
-    cudaMemsetAsync(J[m], 0, p->nao * p->nao * 8, cap);
+    cudaMemsetAsync(p->d_gacc, 0, p->naux_ao * 16, cap);
+    cudaMemsetAsync(p->d_Jacc, 0, p->nao * p->nao * 16, cap);
     for (auto& g : p->groups) {
       launch_pair_precompute(p->orb->dev(), g.d_pairs, (long long)g.counts.size(), g.Ka, g.Kb, g.d_pairrec,
                              g.d_pairab, cap);
@@ -1056,9 +1095,9 @@ lx3c_status lx3c_batch_bind(lx3c_batch* b, const double* const* D, const double*
   launch_persistent(b->d_descs, b->d_work, b->nwork, b->d_counter, b->grid, b->smem, cap);
   b->graph_kernels += 1;
   for (int m = 0; m < nmol; ++m) {
-    dim3 blk(32, 8), grd((unsigned)((b->mols[m]->nao + 31) / 32), (unsigned)((b->mols[m]->nao + 7) / 8));
-    symmetrize<<<grd, blk, 0, cap>>>(J[m], b->mols[m]->nao);
-    b->graph_kernels += 1;
+    launch_fix_finish(b->mols[m]->d_gacc, b->mols[m]->naux_ao, gamma[m], cap);
+    launch_fix_finish_J(b->mols[m]->d_Jacc, b->mols[m]->nao, J[m], cap);
+    b->graph_kernels += 2;
   }
   cudaError_t ce = cudaStreamEndCapture(cap, &b->graph);
   if (ce != cudaSuccess) {

@@ -24,6 +24,7 @@
 // memory and no atomics are needed.
 #include <cuda_runtime.h>
 
+#include "fixed128.cuh"
 #include "lx3c_internal.h"
 
 namespace lx3c {
@@ -743,8 +744,8 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
         }
         if (k < nch) s0 += part[(t * 3 + ax) * nch + k];
         const double s = s0 + s1;
-        atomicAdd(d.grad + 3 * tatom + ax, s);
-        atomicAdd(d.grad + 3 * __ldg(d.aux_atom + aux0 + t) + ax, -s);
+        fix_add(d.facc + 2 * (3 * tatom + ax), s);
+        fix_add(d.facc + 2 * (3 * __ldg(d.aux_atom + aux0 + t) + ax), -s);
       }
       return;
     }
@@ -827,12 +828,12 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       double* Ds = sm + d.dscr;
       double* Cs = Ds + nAB;
       const int sA = d.orient ? 1 : nB, sB = d.orient ? nA : 1;  // storage index of (A, B)
-      if (d.gamma)
+      if (d.gacc)
         for (int s = tid; s < nAB; s += kThreads) {
           const int A = s / nB, B = s - A * nB;
           Ds[A * sA + B * sB] = __ldg(d.D + (long long)(pao.x + A) * d.ldD + pao.y + B);
         }
-      if (d.J)
+      if (d.Jacc)
         for (int i = tid; i < tv * nC; i += kThreads) {
           const int t = i / nC, C = i - t * nC;
           Cs[i] = __ldg(d.cvec + __ldg(d.aux_ao + aux0 + t) + C);
@@ -841,7 +842,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       const Buf cb = cur;
       FDiv fC;
       fC.init(nC);
-      if (d.gamma)
+      if (d.gacc)
         seg_dot(tv * nC, nAB,
                 [&](int o, int r, double acc) {
                   const int t = (int)fC.div(o), C = o - t * nC;
@@ -849,9 +850,9 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
                 },
                 [&](int o, double v) {
                   const int t = (int)fC.div(o), C = o - t * nC;
-                  atomicAdd(d.gamma + __ldg(d.aux_ao + aux0 + t) + C, wg * v);
+                  fix_add(d.gacc + 2 * (__ldg(d.aux_ao + aux0 + t) + C), wg * v);
                 });
-      if (d.J)
+      if (d.Jacc)
         seg_dot(nAB, tv * nC,
                 [&](int o, int r, double acc) {
                   const int t = (int)fC.div(r), C = r - t * nC;
@@ -859,7 +860,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
                 },
                 [&](int o, double v) {
                   const int A = d.orient ? o % nA : o / nB, B = d.orient ? o / nA : o % nB;
-                  atomicAdd(d.J + (long long)(pao.x + A) * d.ldD + pao.y + B, wj * v);
+                  fix_add(d.Jacc + 2 * ((long long)(pao.x + A) * d.ldD + pao.y + B), wj * v);
                 });
       return;
     }

@@ -121,6 +121,12 @@ struct ClassDesc {
   // and the tile's c values [tv*nC padded to 4][8] (zero-padded to 8 columns)
   int nd;
   long long dstride, cstride;
+  // digest 1 and 2 add into exact fixed-point accumulators (fixed128.cuh),
+  // two words per element, instead of the FP64 outputs: gamma [naux_ao],
+  // J [nao][nao], gradient [natom][3]; NULL skips that output
+  unsigned long long* gacc;
+  unsigned long long* Jacc;
+  unsigned long long* facc;
   long long ldD;           // row stride of D and J
   const double* D;
   const double* cvec;

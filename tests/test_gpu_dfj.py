@@ -90,3 +90,22 @@ def test_dfj_256_atoms_sampled(lx):
     plan, g, J = run_gpu(lx, cl, D, c)
     sampled_against_oracle(cl, plan, D, c, g, J, 48, 0, 9, "quad", 1e-12)
     sampled_against_oracle(cl, plan, D, c, g, J, 0, 3, 10, "double", 1e-10)
+
+
+def test_dfj_and_gradient_are_bitwise_reproducible(lx):
+    """gamma, J and dE/dR are summed in exact fixed point, so repeated
+    executes of one plan agree bit for bit whatever order the tiles finish in."""
+    cl = W.cluster((2, 2, 1), W.ORB_RECIPE_SMALL, W.AUX_RECIPE_GRAD, seed=W.SEED_BASE + 50)
+    D, c = inputs(cl, 11)
+    Dt, ct = torch.tensor(D, device="cuda"), torch.tensor(c, device="cuda")
+    plan = lx.DFJPlan(cl.orb, cl.aux, 1e-12, gradient=True)
+    runs = []
+    for _ in range(3):
+        g, J = plan.execute(Dt, ct)
+        G = plan.gradient(Dt, ct)
+        torch.cuda.synchronize()
+        runs.append((g.cpu().numpy().copy(), J.cpu().numpy().copy(), G.cpu().numpy().copy()))
+    for r in runs[1:]:
+        for a, b in zip(r, runs[0]):
+            assert np.array_equal(a, b)
+    assert np.array_equal(runs[0][1], runs[0][1].T)
