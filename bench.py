@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--naux", type=int, default=512)
     ap.add_argument("--product-k", action="store_true", help="read K_ab as (K_a, K_b) = (K_ab, 1)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-hints", action="store_true", help="ignore the package's tuned tile-shape hints")
+    ap.add_argument("--no-hints", action="store_true", help="ignore the package's tuned tile-shape and HRR hints")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--per-class-out", default=None, help="write the per-class table to this JSON file")
@@ -181,9 +181,11 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(dev)
     classes = class_list(args)
     t0 = time.time()
-    args.hints = 0
+    args.hints = args.hrr_hints = 0
     if not args.no_hints and os.path.exists(lx.HINTS_GB300):
         args.hints = lx.load_shape_hints(lx.HINTS_GB300)
+    if not args.no_hints and os.path.exists(lx.HRR_HINTS_GB300):
+        args.hrr_hints = lx.load_hrr_hints(lx.HRR_HINTS_GB300)
     plans = build_plans(classes, args, rank)
     maxtot = max(p["plan"].total for p in plans)
     out = torch.empty(maxtot, dtype=torch.float64, device=dev)
@@ -479,7 +481,7 @@ def run_extras(args, dev):
     out = {}
     names = [] if args.extras == "none" else [x for x in args.extras.split(",") if x]
     def peak():
-        runs = [lx.fp64_rate(1 << 16) for _ in range(3)]
+        runs = [lx.fp64_rate(1 << 15) for _ in range(3)]
         g, ms = max(runs)
         return dict(gflops=round(g, 1), ms=round(ms, 2), frac_of_derived=round(g / FP64_PEAK_GFLOPS, 4),
                     method="lx3c_fp64_rate, best of 3")
@@ -584,7 +586,9 @@ def main():
         data="synthetic (per-class sweep recipe, seeded; no public dataset)",
         config=dict(sweep_config(args, classes, world),
                     tile_shapes=("planner default + %d tuned hints (shape_hints_gb300.txt)" % getattr(args, "hints", 0)
-                                 if getattr(args, "hints", 0) else "planner default")),
+                                 if getattr(args, "hints", 0) else "planner default"),
+                    hrr=("1-q rounds + %d tuned 2-q classes (hrr_hints_gb300.txt)" % getattr(args, "hrr_hints", 0)
+                         if getattr(args, "hrr_hints", 0) else "1-q rounds")),
         roofline=res["roofline"], cpu_baseline=cpu, clocks=res["clocks"], gpu_launches=res["launches"],
         fp64_tflops_sweep=round(res["total_flops"] / (res["ms"] / 1e3) / 1e12, 4),
         l3_roofline_frac=res["l3_frac"],

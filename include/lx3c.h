@@ -150,9 +150,10 @@ lx3c_status lx3c_boys(const double* T, int64_t n, int mmax, double* out, void* s
 /*
  * Measured FP64 FMA throughput of the current device (not in the paper; the
  * roofline denominator of the FP64-bound integral kernels): one kernel of
- * `iters` steps of sixteen independent FMA chains per thread, every SM filled,
- * timed with CUDA events on `stream` after a short warm-up launch.
- * *gflops = 2 * 16 * iters * threads / seconds / 1e9; *ms (may be NULL) = the
+ * `iters` steps of an 8 x 8 register outer product per thread (64 independent
+ * FMAs on 16 operands read from shared memory, as in a DGEMM), every SM
+ * filled, timed with CUDA events on `stream` after a short warm-up launch.
+ * *gflops = 2 * 64 * iters * threads / seconds / 1e9; *ms (may be NULL) = the
  * timed launch's duration.  Allocates and frees a small device buffer and
  * synchronises `stream`.  LX3C_EINVAL for iters < 1 or a NULL gflops.
  */
@@ -179,6 +180,24 @@ lx3c_status lx3c_class_flops(int la, int lb, int lc, int Kab, int Kc, int bra_pu
  * Both return LX3C_EINVAL for arguments out of range.
  */
 lx3c_status lx3c_shape_hint(int la, int lb, int lc, int bra_pure, int kab, int kc, int ctas_per_sm);
+
+/*
+ * HRR variant of class (la, lb | lc) as the planner orients it (Sec. 2.5.5):
+ * variant 0 moves one quantum per round (Eq. hrr, lb rounds with a barrier
+ * each, the fewest FLOPs); variant 1 moves two per round,
+ *   (a, b+1_i+1_k) = (a+1_i+1_k, b) + AB_i (a+1_k, b) + AB_k (a+1_i, b) + AB_i AB_k (a, b),
+ * with one 1-q round last when lb is odd (lb/2 + lb%2 rounds, more FLOPs, no
+ * first-round intermediates); -1 removes the hint (variant 0).  Read by later
+ * plans; process-wide, thread-safe.  LX3C_EINVAL for arguments out of range.
+ */
+lx3c_status lx3c_hrr_hint(int la, int lb, int lc, int bra_pure, int variant);
+/* Host self-check of that variant's tables (no device needed): the table
+ * invariants of lx3c_class_tables_check, then the HRR rows applied to moment
+ * integrals int (x-A)^a (x-B)^b w(x) dx, for which Eq. hrr is exact;
+ * *max_rel_err = the largest error against their closed form relative to
+ * the sum of its term magnitudes. */
+lx3c_status lx3c_hrr_tables_check(int la, int lb, int lc, int bra_pure, int variant, const double* AB,
+                                  double* max_rel_err);
 
 /*
  * Accuracy settings (not in the paper), process-wide and thread-safe, read
@@ -355,7 +374,16 @@ void lx3c_dfj_destroy(lx3c_dfj* plan);
  *   as it was).  Blocked right-looking, 64-wide panels, FP64 throughout.
  *   info (device int32, may be NULL) is set to 0, or to the 1-based index of
  *   the first non-positive pivot (the factor then holds NaN from there on).
- *   Asynchronous on `stream`; LX3C_EINVAL for n < 1, lda < n or a NULL A.
+ *   drop_tol = 0: info gets the first non-positive pivot as above.
+ *   drop_tol in (0, 1): a pivot at or below drop_tol times A's original
+ *   diagonal element marks that function as linearly dependent on the
+ *   earlier ones (the usual treatment of a near-singular fitting metric):
+ *   its diagonal entry becomes +inf and its column below the diagonal 0, so
+ *   lx3c_cholesky_solve gives it a zero coefficient; info gets the number of
+ *   functions dropped.  This mode takes n doubles of stream-ordered scratch
+ *   (cudaMallocAsync).
+ *   Asynchronous on `stream`; LX3C_EINVAL for n < 1, lda < n, a NULL A or
+ *   drop_tol outside [0, 1).
  * lx3c_cholesky_solve: B <- (L L^T)^{-1} B with L from lx3c_cholesky and B
  *   (device, n x nrhs row-major, the nrhs right-hand sides contiguous per
  *   row) overwritten.  Asynchronous on `stream`.
@@ -369,7 +397,7 @@ lx3c_status lx3c_metric_plan(lx3c_metric** out, const lx3c_basis* aux, void* str
 lx3c_status lx3c_metric_execute(lx3c_metric* plan, double* V, void* stream);
 lx3c_status lx3c_metric_info(const lx3c_metric* plan, double* out, int n);
 void lx3c_metric_destroy(lx3c_metric* plan);
-lx3c_status lx3c_cholesky(double* A, int64_t n, int64_t lda, int32_t* info, void* stream);
+lx3c_status lx3c_cholesky(double* A, int64_t n, int64_t lda, double drop_tol, int32_t* info, void* stream);
 lx3c_status lx3c_cholesky_solve(const double* L, int64_t n, int64_t lda, double* B, int64_t nrhs, void* stream);
 lx3c_status lx3c_dfj_coulomb(lx3c_dfj* plan, const double* L, int64_t lda, const double* D, double* gamma,
                              double* c, double* J, void* stream);

@@ -337,17 +337,18 @@ class MetricPlan:
             self.handle = None
 
 
-def cholesky(A, stream=None):
+def cholesky(A, drop_tol=0.0, stream=None):
     """In-place lower Cholesky factor of the symmetric positive definite CUDA
-    float64 matrix A (lx3c_cholesky); returns (A, info) with info the 1-based
-    first non-positive pivot or 0 (reading info synchronises)."""
+    float64 matrix A (lx3c_cholesky); returns (A, info): with drop_tol = 0 the
+    1-based first non-positive pivot or 0, else the number of functions
+    dropped as linearly dependent (reading info synchronises)."""
     torch = _torch()
     n = A.shape[0]
     if A.dtype != torch.float64 or not A.is_cuda or A.dim() != 2 or A.shape[1] < n or A.stride(1) != 1:
         raise LibraryError("cholesky: A must be a row-major float64 CUDA matrix")
     info = torch.zeros(1, dtype=torch.int32, device=A.device)
-    check(_lib.load().lx3c_cholesky(ctypes.c_void_p(A.data_ptr()), n, A.stride(0), ctypes.c_void_p(info.data_ptr()),
-                                    _stream_handle(stream)), "lx3c_cholesky")
+    check(_lib.load().lx3c_cholesky(ctypes.c_void_p(A.data_ptr()), n, A.stride(0), float(drop_tol),
+                                    ctypes.c_void_p(info.data_ptr()), _stream_handle(stream)), "lx3c_cholesky")
     return A, int(info.item())
 
 
@@ -477,6 +478,12 @@ def shape_hint(la, lb, lc, kab, kc=1, ctas_per_sm=2, bra_pure=True):
     check(_lib.load().lx3c_shape_hint(la, lb, lc, int(bool(bra_pure)), kab, kc, ctas_per_sm), "lx3c_shape_hint")
 
 
+def hrr_hint(la, lb, lc, variant, bra_pure=True):
+    """HRR variant of class (la, lb | lc) for later plans: 0 one quantum per
+    round, 1 two quanta per round, -1 remove the hint (lx3c_hrr_hint)."""
+    check(_lib.load().lx3c_hrr_hint(la, lb, lc, int(bool(bra_pure)), int(variant)), "lx3c_hrr_hint")
+
+
 def shape_query(la, lb, lc, kab, kc=1, naux=512, ctas_per_sm=0, bra_pure=True):
     """(T, G, mode, smem bytes) the planner gives the class (lx3c_shape_query)."""
     out = np.zeros(4, np.int32)
@@ -544,6 +551,24 @@ def schwarz_factors(orb, pairs, aux, kets):
         check(L.lx3c_schwarz_aux(l, k, ptr(e), ptr(c), ctypes.byref(q)), "lx3c_schwarz_aux")
         qa[i] = q.value
     return qp, qa
+
+
+HRR_HINTS_GB300 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "hrr_hints_gb300.txt")
+
+
+def load_hrr_hints(path=HRR_HINTS_GB300):
+    """Apply an HRR-variant hints file ("la lb lc bra_pure variant" per line,
+    '#' comments); returns the number of hints applied."""
+    n = 0
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if not line:
+                continue
+            la, lb, lc, pure, v = (int(x) for x in line)
+            hrr_hint(la, lb, lc, v, bool(pure))
+            n += 1
+    return n
 
 
 def class_flops(la, lb, lc, Kab, Kc=1, bra_pure=True):

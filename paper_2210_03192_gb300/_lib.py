@@ -70,14 +70,16 @@ EXPORTS = {
     "lx3c_metric_execute": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "lx3c_metric_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lx3c_metric_destroy": (None, [ctypes.c_void_p]),
-    "lx3c_cholesky": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
-                                     ctypes.c_void_p]),
+    "lx3c_cholesky": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
     "lx3c_cholesky_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_void_p]),
     "lx3c_dfj_coulomb": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 5),
     "lx3c_cvrr2_expansion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "lx3c_shape_hint": (ctypes.c_int, [ctypes.c_int] * 7),
+    "lx3c_hrr_hint": (ctypes.c_int, [ctypes.c_int] * 5),
+    "lx3c_hrr_tables_check": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.c_void_p, c_f64p]),
     "lx3c_set_orientation_threshold": (ctypes.c_int, [ctypes.c_double]),
     "lx3c_set_compensation": (ctypes.c_int, [ctypes.c_int]),
     "lx3c_class_tables_check": (ctypes.c_int, [ctypes.c_int] * 4),

@@ -100,7 +100,7 @@ lx3c_status device_state(DevState** out) {
 
 lx3c_status device_class(DevState* s, const ClassTables& ct, DevClass** out) {
   std::lock_guard<std::mutex> lk(g_mu);
-  auto key = std::make_tuple(ct.la, ct.lb, ct.lc, ct.bra_pure);
+  auto key = std::make_tuple(ct.la, ct.lb, ct.lc, ct.bra_pure * 2 + ct.hrr2);
   auto it = s->classes.find(key);
   if (it != s->classes.end()) {
     *out = &it->second;
@@ -160,7 +160,7 @@ void class_blob_pointers(DevClass& dc, const void* dev_blob, const size_t f[16])
   dc.pal = (const double*)(b + f[6]);
   dc.kptr = (const int*)(b + f[7]);
   dc.kent = (const int2*)(b + f[8]);
-  dc.htab = (const int4*)(b + f[9]);
+  dc.htab = (const uint4*)(b + f[9]);
   dc.baptr = (const int*)(b + f[10]);
   dc.baent = (const int2*)(b + f[11]);
   dc.bbptr = (const int*)(b + f[12]);
@@ -186,8 +186,9 @@ void fill_desc_common(ClassDesc& d, const ClassTables& ct, const DevClass& dc, c
   d.nW = ct.NW;
   d.ngt = ct.nkrow * ct.ncc;
   d.nkrow = ct.nkrow;
-  for (int j = 0; j <= ct.lb; ++j) d.hrows[j] = ct.hrows[j];
-  for (int j = 0; j <= ct.lb + 1; ++j) d.hstart[j] = ct.hstart[j];
+  d.nhrr = ct.nhrr;
+  for (int j = 0; j <= ct.nhrr; ++j) d.hrows[j] = ct.hrows[j];
+  for (int j = 0; j <= ct.nhrr + 1; ++j) d.hstart[j] = ct.hstart[j];
   d.nbA = ct.nbA; d.nbB = ct.nbB;
   d.vtab = dc.vtab; d.wtab = dc.wtab; d.atab = dc.atab; d.gptr = dc.gptr; d.gterm = dc.gterm;
   d.gdst = dc.gdst; d.pal = dc.pal; d.kptr = dc.kptr; d.kent = dc.kent; d.htab = dc.htab;
@@ -673,6 +674,30 @@ lx3c_status lx3c_set_orientation_threshold(double amp_max) {
 lx3c_status lx3c_set_compensation(int bits) {
   if (bits < 0 || bits > 3) return fail(LX3C_EINVAL, "set_compensation: bits must be in 0..3");
   g_comp_bits.store(bits);
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_hrr_tables_check(int la, int lb, int lc, int bra_pure, int variant, const double* AB,
+                                  double* max_rel_err) {
+  if (!AB || !max_rel_err || la < 0 || lb < 0 || lc < 0 || la > LX3C_LMAX_ORB + 1 || lb > LX3C_LMAX_ORB + 1 ||
+      lc > LX3C_LMAX_AUX || variant < 0 || variant > 1)
+    return fail(LX3C_EINVAL, "hrr_tables_check: bad argument");
+  try {
+    const ClassTables& ct = class_tables_variant(la, lb, lc, bra_pure ? 1 : 0, variant);
+    const std::string msg = check_class_tables(ct);
+    if (!msg.empty()) return fail(LX3C_EINVAL, "class tables: " + msg);
+    *max_rel_err = hrr_moment_error(ct, AB);
+  } catch (std::exception& e) {
+    return fail(LX3C_ENOTSUP, e.what());
+  }
+  return LX3C_OK;
+}
+
+lx3c_status lx3c_hrr_hint(int la, int lb, int lc, int bra_pure, int variant) {
+  if (la < 0 || lb < 0 || lc < 0 || la > LX3C_LMAX_ORB + 1 || lb > LX3C_LMAX_ORB + 1 || lc > LX3C_LMAX_AUX ||
+      variant < -1 || variant > 1)
+    return fail(LX3C_EINVAL, "hrr_hint: bad argument");
+  set_hrr_hint(la, lb, lc, bra_pure, variant);
   return LX3C_OK;
 }
 

@@ -327,9 +327,19 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
         const long long r = pair * d.Kab_rec + __ldg(d.primidx + sp.y + g);
         sm[d.pair_base + i] = d.pairrec[r * kPairRec + fs];
       }
-      if (tid < 3) {
-        const double ab = d.pairab[pair * 3 + tid];
-        sm[d.ab_base + tid] = d.orient ? -ab : ab;
+      if (tid < 13) {
+        // the HRR coefficients: 1, AB_i, 2 AB_i, AB_i^2, AB_x AB_y, AB_x AB_z, AB_y AB_z
+        const double sg = d.orient ? -1.0 : 1.0;
+        const double x = sg * d.pairab[pair * 3], y = sg * d.pairab[pair * 3 + 1], z = sg * d.pairab[pair * 3 + 2];
+        const double ab[3] = {x, y, z};
+        double v = 1.0;
+        if (tid >= 1 && tid <= 3) v = ab[tid - 1];
+        else if (tid >= 4 && tid <= 6) v = 2.0 * ab[tid - 4];
+        else if (tid >= 7 && tid <= 9) v = ab[tid - 7] * ab[tid - 7];
+        else if (tid == 10) v = x * y;
+        else if (tid == 11) v = x * z;
+        else if (tid == 12) v = y * z;
+        sm[d.ab_base + tid] = v;
       }
       for (int i = tid; i < tv * auxsz; i += kThreads) {
         int t = i / auxsz, r = i - t * auxsz;
@@ -579,27 +589,34 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       }
     }
     __syncthreads();
-    // ---- HRR (Eq. hrr), level by level
-    for (int j = 1; j <= d.lb; ++j) {
+    // ---- HRR (Eq. hrr) round by round: each row is dst = sum_t coef_t src_t
+    // over 2 terms (one quantum moved, Eq. hrr) or 3-4 terms (two quanta,
+    // Sec. 2.5.5), the coefficients products of AB components
+    for (int j = 1; j <= d.nhrr; ++j) {
       FDiv fX, fC;
       const int nx = d.hrows[j] * d.nC;
       fX.init(nx);
       fC.init(d.nC);
       const unsigned n = (unsigned)(T * nx);
       const Buf hi = d.H[j - 1], ho = d.H[j];
+      const double* abp = sm + d.ab_base;
       for (unsigned w = tid; w < n; w += kThreads) {
         int t, x;
         dec2(w, mode, fT, fX, t, x);
         if (t >= tv) continue;
         const int r = (int)fC.div(x), C = x - r * d.nC;
-        const int4 e = __ldg(d.htab + d.hstart[j] + r);
-        const double v = fma(sm[d.ab_base + e.w], sm[BUF_T(hi, e.z * d.nC + C, t)], sm[BUF_T(hi, e.y * d.nC + C, t)]);
-        sm[BUF_T(ho, e.x * d.nC + C, t)] = v;
+        const uint4 e = __ldg(d.htab + d.hstart[j] + r);
+        const unsigned nt = e.x >> 16;
+        double v = fma(abp[(e.w >> 4) & 0xF], sm[BUF_T(hi, (int)(e.y >> 16) * d.nC + C, t)],
+                       sm[BUF_T(hi, (int)(e.y & 0xFFFF) * d.nC + C, t)]);
+        if (nt > 2) v = fma(abp[(e.w >> 8) & 0xF], sm[BUF_T(hi, (int)(e.z & 0xFFFF) * d.nC + C, t)], v);
+        if (nt > 3) v = fma(abp[(e.w >> 12) & 0xF], sm[BUF_T(hi, (int)(e.z >> 16) * d.nC + C, t)], v);
+        sm[BUF_T(ho, (int)(e.x & 0xFFFF) * d.nC + C, t)] = v;
       }
       __syncthreads();
     }
     // ---- optional solid-harmonic bra
-    Buf cur = d.H[d.lb];
+    Buf cur = d.H[d.nhrr];
     if (d.nbA) {
       FDiv fX, fC, fB;
       const int nx = d.nbA * d.nC;

@@ -64,8 +64,9 @@ struct ClassDesc {
   int nW;                  // weight items (= NW)
   int ngt;                 // gather targets
   int nkrow;               // rows (bra Cartesian functions) entering the ket transform
-  int hrows[kMaxLev + 1];  // rows per HRR level (level 0 = nkrow)
-  int hstart[kMaxLev + 1]; // first htab entry of level j (j >= 1)
+  int nhrr;                // HRR rounds (lb for 1-q HRR; lb/2 + lb%2 for 2-q)
+  int hrows[kMaxLev + 1];  // rows per HRR round (round 0 = nkrow)
+  int hstart[kMaxLev + 1]; // first htab entry of round r (r >= 1)
   int nbA, nbB;            // bra transform output rows (A,b) and (A,B), 0 if none
   // tables (device)
   const uint4* vtab;       // VRR1 items
@@ -82,7 +83,9 @@ struct ClassDesc {
   const double* pal;       // coefficient palette
   const int* kptr;         // ket CSR by C
   const int2* kent;        // (c, coef_id)
-  const int4* htab;        // HRR rows: dst_row, hi_row, lo_row, axis
+  // HRR rows {dst | nterm << 16, src0 | src1 << 16, src2 | src3 << 16, 4-bit
+  // codes of the terms' AB-product coefficients}: dst = sum_t coef_t src_t
+  const uint4* htab;
   const int* baptr;        // bra A transform CSR by A: entries (a, coef_id)
   const int2* baent;
   const int* bbptr;        // bra B transform CSR by B
@@ -177,8 +180,10 @@ struct ClassTables {
   std::vector<int> kptr;
   std::vector<int2> kent;
   int nkrow;
+  int nhrr = 0, hrr2 = 0;      // HRR rounds; 1 if rounds move two quanta (Sec. 2.5.5)
+  std::vector<int4> erow_xyz;  // Cartesian exponents of the nkrow round-0 rows
   std::vector<int> hrows, hstart;
-  std::vector<int4> htab;
+  std::vector<uint4> htab;
   std::vector<int> baptr, bbptr;
   std::vector<int2> baent, bbent;
   int nbA, nbB;
@@ -204,7 +209,7 @@ struct DevClass {
   const double* pal;
   const int* kptr;
   const int2* kent;
-  const int4* htab;
+  const uint4* htab;
   const int* baptr;
   const int2* baent;
   const int* bbptr;
@@ -235,7 +240,10 @@ std::vector<char> class_blob(const ClassTables& ct, size_t offs[16]);
 void class_blob_pointers(DevClass& dc, const void* dev_blob, const size_t offs[16]);
 
 // planner entry points (plan.cu)
-const ClassTables& class_tables(int la, int lb, int lc, int bra_pure);
+const ClassTables& class_tables(int la, int lb, int lc, int bra_pure);  // HRR variant from the hints
+const ClassTables& class_tables_variant(int la, int lb, int lc, int bra_pure, int hrr2);
+void set_hrr_hint(int la, int lb, int lc, int bra_pure, int variant);  // variant < 0 removes the hint
+int hrr_variant(int la, int lb, int lc, int bra_pure);
 std::vector<double> solid_matrix(int l);   // [(m+l)*ncart(l) + c]
 int ncart(int l);
 int cart_index(int x, int y, int z);       // index of (x,y,z) within its shell
@@ -258,6 +266,9 @@ void set_digest_scratch(ClassDesc& d);
 // d.smem_doubles).
 int place_epilogue_scratch(ClassDesc& d, long long need);
 std::string check_class_tables(const ClassTables& ct);  // "" when every table invariant holds
+// Largest relative error of the class's HRR tables applied to moment
+// integrals (exact for any weight), see lx3c_hrr_tables_check.
+double hrr_moment_error(const ClassTables& ct, const double AB[3]);
 LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit);
 LaunchShape choose_shape_for(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit, int ctas);
 void set_shape_hint(int la, int lb, int lc, int bra_pure, int Kab, int Kc, int ctas);

@@ -64,7 +64,8 @@ constexpr int kTrsmRows = 128; // rows per CTA of the panel solve
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) chol_diag(double* __restrict__ A, long long lda, long long k, int nb,
-                                                 int* __restrict__ info) {
+                                                 int* __restrict__ info, const double* __restrict__ diag0,
+                                                 double drop_tol) {
   __shared__ double s[kNB][kNB + 1];
   const int tid = threadIdx.x;
   for (int idx = tid; idx < nb * nb; idx += 256) {
@@ -75,11 +76,23 @@ __global__ void __launch_bounds__(256) chol_diag(double* __restrict__ A, long lo
   for (int j = 0; j < nb; ++j) {
     if (tid == 0) {
       double dj = s[j][j];
-      if (!(dj > 0.0)) {  // not positive definite: record the first such pivot, carry NaN on
-        if (info && *info == 0) *info = (int)(k + j + 1);
-        dj = nan("");
+      if (diag0) {
+        // drop mode: a pivot at or below drop_tol of the original diagonal
+        // marks a function dependent on the earlier ones; an infinite pivot
+        // zeroes its column below and its coefficient in the solves
+        if (!(dj > drop_tol * diag0[k + j])) {
+          if (info) ++*info;
+          s[j][j] = __longlong_as_double(0x7FF0000000000000LL);
+        } else {
+          s[j][j] = sqrt(dj);
+        }
+      } else {
+        if (!(dj > 0.0)) {  // not positive definite: record the first such pivot, carry NaN on
+          if (info && *info == 0) *info = (int)(k + j + 1);
+          dj = nan("");
+        }
+        s[j][j] = sqrt(dj);
       }
-      s[j][j] = sqrt(dj);
     }
     __syncthreads();
     const double piv = s[j][j];
@@ -254,11 +267,17 @@ cudaError_t chol_attributes() {
   return e;
 }
 
-cudaError_t cholesky_launches(double* A, long long n, long long lda, int* info, cudaStream_t st) {
+__global__ void copy_diag(const double* __restrict__ A, long long lda, long long n, double* __restrict__ d) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) d[i] = A[i * lda + i];
+}
+
+cudaError_t cholesky_launches(double* A, long long n, long long lda, int* info, const double* diag0,
+                              double drop_tol, cudaStream_t st) {
   cudaError_t e = chol_attributes();
   for (long long k = 0; k < n && e == cudaSuccess; k += kNB) {
     const int nb = (int)std::min<long long>(kNB, n - k);
-    chol_diag<<<1, 256, 0, st>>>(A, lda, k, nb, info);
+    chol_diag<<<1, 256, 0, st>>>(A, lda, k, nb, info, diag0, drop_tol);
     e = cudaGetLastError();
     const long long m = n - k - nb;
     if (m <= 0 || e != cudaSuccess) continue;
@@ -477,11 +496,20 @@ lx3c_status lx3c_metric_info(const lx3c_metric* p, double* out, int n) {
   return LX3C_OK;
 }
 
-lx3c_status lx3c_cholesky(double* A, int64_t n, int64_t lda, int32_t* info, void* stream) {
+lx3c_status lx3c_cholesky(double* A, int64_t n, int64_t lda, double drop_tol, int32_t* info, void* stream) {
   if (!A || n < 1 || lda < n) return mfail(LX3C_EINVAL, "cholesky: null matrix, n < 1 or lda < n");
+  if (!(drop_tol >= 0.0 && drop_tol < 1.0)) return mfail(LX3C_EINVAL, "cholesky: drop_tol must be in [0, 1)");
   cudaStream_t st = (cudaStream_t)stream;
   if (info) MCUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
-  MCUDA(cholesky_launches(A, n, lda, info, st));
+  double* diag0 = nullptr;
+  if (drop_tol > 0.0) {
+    MCUDA(cudaMallocAsync(&diag0, (size_t)n * sizeof(double), st));
+    copy_diag<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, lda, n, diag0);
+    MCUDA(cudaGetLastError());
+  }
+  cudaError_t e = cholesky_launches(A, n, lda, info, diag0, drop_tol, st);
+  if (diag0) cudaFreeAsync(diag0, st);
+  MCUDA(e);
   return LX3C_OK;
 }
 

@@ -120,14 +120,15 @@ struct NaBlob {
 
 const NaBlob& na_blob(int la, int lb, int lc, int bra_pure, int split) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int>, NaBlob> cache;
+  static std::map<std::tuple<int, int, int, int, int, int>, NaBlob> cache;
   std::lock_guard<std::mutex> lk(mu);
-  auto key = std::make_tuple(la, lb, lc, bra_pure);
+  const ClassTables* ct[2] = {&class_tables(la, lb, lc, bra_pure), &class_tables(lb, la, lc, bra_pure)};
+  auto key = std::make_tuple(la, lb, lc, bra_pure, ct[0]->hrr2, ct[1]->hrr2);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   NaBlob nb;
   for (int o = 0; o < 1 + split; ++o) {
-    std::vector<char> part = class_blob(class_tables(o ? lb : la, o ? la : lb, lc, bra_pure), nb.offs[o]);
+    std::vector<char> part = class_blob(*ct[o], nb.offs[o]);
     nb.base[o] = (nb.bytes.size() + 255) & ~size_t(255);
     nb.bytes.resize(nb.base[o] + part.size());
     std::memcpy(nb.bytes.data() + nb.base[o], part.data(), part.size());

@@ -104,7 +104,7 @@ unsigned pal_id(std::vector<double>& pal, std::map<double, int>& ids, double v) 
   return id;
 }
 
-ClassTables build(int la, int lb, int lc, int bra_pure) {
+ClassTables build(int la, int lb, int lc, int bra_pure, int hrr2) {
   ClassTables ct;
   ct.la = la; ct.lb = lb; ct.lc = lc; ct.bra_pure = bra_pure;
   const int Lab = la + lb;
@@ -116,48 +116,71 @@ ClassTables build(int la, int lb, int lc, int bra_pure) {
   pal_id(ct.pal, palids, 1.0);  // id 0 is always 1.0
 
   // ---------------- HRR dependency analysis (Eq. hrr) ----------------
-  // nodes (a, b) per level j = |b|; level lb: |a| = la, all (a, b)
-  std::vector<std::vector<std::pair<C3, C3>>> lev(lb + 1);
-  std::vector<std::map<std::pair<C3, C3>, int>> levidx(lb + 1);
-  std::vector<std::map<C3, int>> baxis(lb + 1);
+  // Rounds r = 1..R move q_r quanta from the recurrence centre to the other:
+  // every q_r = 1 (1-q HRR, Eq. hrr), or with hrr2 the 2-quantum transfer of
+  // Sec. 2.5.5 applied twice in one round,
+  //   (a, b+1_i+1_k) = (a+1_i+1_k, b) + AB_i (a+1_k, b) + AB_k (a+1_i, b) + AB_i AB_k (a, b),
+  // with one 1-q round last (topmost) when lb is odd.  Nodes (a, b) of round
+  // r have |b| = the quanta moved so far; the top round holds every (a, b) of
+  // the target, and each round keeps only the nodes the next one reads
+  // (greedy cover: as few lower b's as possible).
+  std::vector<int> step;  // q_r, r = 1..R, bottom-up
+  if (hrr2) {
+    for (int q = 0; q < lb / 2; ++q) step.push_back(2);
+    if (lb & 1) step.push_back(1);
+  } else {
+    for (int q = 0; q < lb; ++q) step.push_back(1);
+  }
+  const int R = (int)step.size();
+  std::vector<int> bl(R + 1, 0);  // |b| of round r
+  for (int r = 1; r <= R; ++r) bl[r] = bl[r - 1] + step[r - 1];
+  std::vector<std::vector<std::pair<C3, C3>>> lev(R + 1);
+  std::vector<std::map<std::pair<C3, C3>, int>> levidx(R + 1);
+  // per needed b of round r: the lower b and the axes (i, k) (k = -1 for 1-q)
+  std::vector<std::map<C3, std::pair<C3, std::pair<int, int>>>> bdec(R + 1);
   for (auto& a : cart(la))
     for (auto& b : cart(lb)) {
-      levidx[lb][{a, b}] = (int)lev[lb].size();
-      lev[lb].push_back({a, b});
+      levidx[R][{a, b}] = (int)lev[R].size();
+      lev[R].push_back({a, b});
     }
-  for (int j = lb; j >= 1; --j) {
-    // choose, for every b on level j, the axis to lower: greedy cover of the
-    // needed b's by as few predecessors b-1_i as possible
+  auto add = [](C3 x, int i, int k) {
+    if (i >= 0) x.v[i]++;
+    if (k >= 0) x.v[k]++;
+    return x;
+  };
+  for (int r = R; r >= 1; --r) {
+    const int q = step[r - 1];
     std::set<C3> need;
-    for (auto& n : lev[j]) need.insert(n.second);
+    for (auto& n : lev[r]) need.insert(n.second);
     while (!need.empty()) {
       C3 best{{0, 0, 0}};
       int bestcount = -1;
-      for (auto& bp : cart(j - 1)) {
+      for (auto& bp : cart(bl[r - 1])) {
         int cnt = 0;
-        for (int i = 0; i < 3; ++i) {
-          C3 b = bp;
-          b.v[i]++;
-          if (need.count(b)) ++cnt;
-        }
+        for (int i = 0; i < 3; ++i)
+          for (int k = (q == 2 ? i : -1); k < (q == 2 ? 3 : 0); ++k)
+            if (need.count(add(bp, i, k))) ++cnt;
         if (cnt > bestcount) { bestcount = cnt; best = bp; }
       }
-      for (int i = 0; i < 3; ++i) {
-        C3 b = best;
-        b.v[i]++;
-        if (need.count(b)) { baxis[j][b] = i; need.erase(b); }
-      }
+      for (int i = 0; i < 3; ++i)
+        for (int k = (q == 2 ? i : -1); k < (q == 2 ? 3 : 0); ++k) {
+          C3 b = add(best, i, k);
+          if (need.count(b)) { bdec[r][b] = {best, {i, k}}; need.erase(b); }
+        }
     }
     std::set<std::pair<C3, C3>> prev;
-    for (auto& n : lev[j]) {
-      int i = baxis[j][n.second];
-      C3 a1 = n.first, bm = n.second;
-      a1.v[i]++;
-      bm.v[i]--;
-      prev.insert({a1, bm});
-      prev.insert({n.first, bm});
+    for (auto& n : lev[r]) {
+      const auto& dec = bdec[r][n.second];
+      const C3& bp = dec.first;
+      const int i = dec.second.first, k = dec.second.second;
+      prev.insert({add(n.first, i, k), bp});
+      prev.insert({n.first, bp});
+      if (k >= 0) {
+        prev.insert({add(n.first, i, -1), bp});
+        prev.insert({add(n.first, k, -1), bp});
+      }
     }
-    // order level j-1 nodes: by |a|, then a, then b
+    // order the lower round's nodes: by |a|, then a, then b
     std::vector<std::pair<C3, C3>> pv(prev.begin(), prev.end());
     std::sort(pv.begin(), pv.end(), [](const std::pair<C3, C3>& x, const std::pair<C3, C3>& y) {
       if (x.first.l() != y.first.l()) return x.first.l() < y.first.l();
@@ -167,29 +190,64 @@ ClassTables build(int la, int lb, int lc, int bra_pure) {
       return cart_index(x.second.v[0], x.second.v[1], x.second.v[2]) <
              cart_index(y.second.v[0], y.second.v[1], y.second.v[2]);
     });
-    lev[j - 1] = pv;
-    for (size_t r = 0; r < pv.size(); ++r) levidx[j - 1][pv[r]] = (int)r;
+    lev[r - 1] = pv;
+    for (size_t n = 0; n < pv.size(); ++n) levidx[r - 1][pv[n]] = (int)n;
   }
-  // e0 rows (level 0): needed bra functions (a, 0)
+  // e0 rows (round 0): needed bra functions (a, 0)
   std::vector<C3> erows;
   for (auto& n : lev[0]) erows.push_back(n.first);
   ct.nkrow = (int)erows.size();
-  ct.hrows.assign(lb + 1, 0);
-  ct.hstart.assign(lb + 2, 0);
+  for (auto& e : erows) ct.erow_xyz.push_back(int4{e.v[0], e.v[1], e.v[2], 0});
+  ct.nhrr = R;
+  ct.hrr2 = hrr2;
+  ct.hrows.assign(R + 1, 0);
+  ct.hstart.assign(R + 2, 0);
   ct.hrows[0] = ct.nkrow;
-  for (int j = 1; j <= lb; ++j) {
-    ct.hstart[j] = (int)ct.htab.size();
-    ct.hrows[j] = (int)lev[j].size();
-    for (size_t r = 0; r < lev[j].size(); ++r) {
-      auto& n = lev[j][r];
-      int i = baxis[j][n.second];
-      C3 a1 = n.first, bm = n.second;
-      a1.v[i]++;
-      bm.v[i]--;
-      ct.htab.push_back(int4{(int)r, levidx[j - 1].at({a1, bm}), levidx[j - 1].at({n.first, bm}), i});
+  // row = {dst | nterm << 16, src0 | src1 << 16, src2 | src3 << 16, 4-bit
+  // coefficient codes}; codes index the tile's AB products: 0 one, 1..3 AB_i,
+  // 4..6 2 AB_i, 7..9 AB_i^2, 10 AB_x AB_y, 11 AB_x AB_z, 12 AB_y AB_z
+  auto pcode = [](int i, int k) {
+    if (i == k) return 7 + i;
+    const int lo = std::min(i, k), hi = std::max(i, k);
+    return lo == 0 ? (hi == 1 ? 10 : 11) : 12;
+  };
+  for (int r = 1; r <= R; ++r) {
+    ct.hstart[r] = (int)ct.htab.size();
+    ct.hrows[r] = (int)lev[r].size();
+    std::vector<std::pair<int, uint4>> rows;
+    for (size_t n = 0; n < lev[r].size(); ++n) {
+      const auto& node = lev[r][n];
+      const auto& dec = bdec[r][node.second];
+      const C3& bp = dec.first;
+      const int i = dec.second.first, k = dec.second.second;
+      const C3& a = node.first;
+      unsigned src[4] = {0, 0, 0, 0}, code[4] = {0, 0, 0, 0};
+      int nt;
+      auto at = [&](const C3& x) { return (unsigned)levidx[r - 1].at({x, bp}); };
+      if (k < 0) {
+        src[0] = at(add(a, i, -1)); code[0] = 0;
+        src[1] = at(a); code[1] = 1 + i;
+        nt = 2;
+      } else if (i == k) {
+        src[0] = at(add(a, i, i)); code[0] = 0;
+        src[1] = at(add(a, i, -1)); code[1] = 4 + i;
+        src[2] = at(a); code[2] = pcode(i, i);
+        nt = 3;
+      } else {
+        src[0] = at(add(a, i, k)); code[0] = 0;
+        src[1] = at(add(a, k, -1)); code[1] = 1 + i;
+        src[2] = at(add(a, i, -1)); code[2] = 1 + k;
+        src[3] = at(a); code[3] = pcode(i, k);
+        nt = 4;
+      }
+      rows.push_back({nt, uint4{(unsigned)n | ((unsigned)nt << 16), src[0] | (src[1] << 16), src[2] | (src[3] << 16),
+                                code[0] | (code[1] << 4) | (code[2] << 8) | (code[3] << 12)}});
     }
+    // rows with the same term count together, so that a warp's lanes share it
+    std::stable_sort(rows.begin(), rows.end(), [](auto& x, auto& y) { return x.first < y.first; });
+    for (auto& rw : rows) ct.htab.push_back(rw.second);
   }
-  ct.hstart[lb + 1] = (int)ct.htab.size();
+  ct.hstart[R + 1] = (int)ct.htab.size();
 
   // ---------------- VRR1 buffer and items (Eq. vrr1) ----------------
   std::vector<int> voff(Lab + 2, 0);
@@ -392,7 +450,7 @@ ClassTables build(int la, int lb, int lc, int bra_pure) {
   ct.flops_prim = fp;
   double fc = 2.0 * ct.gterm.size();
   fc += 2.0 * ct.kent.size() * ct.nkrow;
-  for (int j = 1; j <= lb; ++j) fc += 2.0 * ct.hrows[j] * ct.nC;
+  for (const uint4& h : ct.htab) fc += 2.0 * ((h.x >> 16) - 1) * ct.nC;
   auto bra = [&](const std::vector<int>& ptr, const std::vector<int2>& ent, int nother) {
     double f = 0;
     for (size_t A = 0; A + 1 < ptr.size(); ++A) {
@@ -410,14 +468,35 @@ ClassTables build(int la, int lb, int lc, int bra_pure) {
 
 }  // namespace
 
-const ClassTables& class_tables(int la, int lb, int lc, int bra_pure) {
-  static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int>, ClassTables> cache;
-  std::lock_guard<std::mutex> lk(mu);
+namespace {
+std::mutex g_hrr_mu;
+std::map<std::tuple<int, int, int, int>, int> g_hrr_hints;  // (la, lb, lc, pure) -> 0: 1-q, 1: 2-q HRR
+}  // namespace
+
+void set_hrr_hint(int la, int lb, int lc, int bra_pure, int variant) {
+  std::lock_guard<std::mutex> lk(g_hrr_mu);
   auto key = std::make_tuple(la, lb, lc, bra_pure ? 1 : 0);
+  if (variant < 0) g_hrr_hints.erase(key); else g_hrr_hints[key] = variant;
+}
+
+int hrr_variant(int la, int lb, int lc, int bra_pure) {
+  std::lock_guard<std::mutex> lk(g_hrr_mu);
+  auto it = g_hrr_hints.find(std::make_tuple(la, lb, lc, bra_pure ? 1 : 0));
+  return it == g_hrr_hints.end() ? 0 : it->second;
+}
+
+const ClassTables& class_tables_variant(int la, int lb, int lc, int bra_pure, int hrr2) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int>, ClassTables> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(la, lb, lc, bra_pure ? 1 : 0, (hrr2 && lb >= 2) ? 1 : 0);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  return cache.emplace(key, build(la, lb, lc, bra_pure ? 1 : 0)).first->second;
+  return cache.emplace(key, build(la, lb, lc, bra_pure ? 1 : 0, std::get<4>(key))).first->second;
+}
+
+const ClassTables& class_tables(int la, int lb, int lc, int bra_pure) {
+  return class_tables_variant(la, lb, lc, bra_pure, hrr_variant(la, lb, lc, bra_pure));
 }
 
 // Invariants of a class's host tables; empty string when they all hold.
@@ -493,14 +572,16 @@ std::string check_class_tables(const ClassTables& ct) {
   for (size_t q = 0; q < ct.kent.size(); ++q)
     if (ct.kent[q].x < 0 || ct.kent[q].x >= ct.ncc || ct.kent[q].y < 0 || ct.kent[q].y >= (int)ct.pal.size())
       return bad("ket entry", (long long)q);
-  // HRR: level j rows built from rows of level j-1
-  for (int j = 1; j <= ct.lb; ++j)
-    for (int i = ct.hstart[j]; i < ct.hstart[j + 1]; ++i) {
-      const int4 h = ct.htab[i];
-      if (h.x < 0 || h.x >= ct.hrows[j] || h.y < 0 || h.y >= ct.hrows[j - 1] || h.z < 0 || h.z >= ct.hrows[j - 1] ||
-          h.w < 0 || h.w > 2)
-        return bad("HRR row", i);
+  // HRR: round r rows built from rows of round r-1, 2..4 terms, codes < 13
+  for (int r = 1; r <= ct.nhrr; ++r)
+    for (int i = ct.hstart[r]; i < ct.hstart[r + 1]; ++i) {
+      const uint4 h = ct.htab[i];
+      const unsigned nt = h.x >> 16, src[4] = {h.y & 0xFFFF, h.y >> 16, h.z & 0xFFFF, h.z >> 16};
+      if ((int)(h.x & 0xFFFF) >= ct.hrows[r] || nt < 2 || nt > 4 || (h.w & 0xF) != 0) return bad("HRR row", i);
+      for (unsigned t = 0; t < nt; ++t)
+        if ((int)src[t] >= ct.hrows[r - 1] || ((h.w >> (4 * t)) & 0xF) > 12) return bad("HRR term", i);
     }
+  if (ct.nhrr != (ct.hrr2 ? ct.lb / 2 + (ct.lb & 1) : ct.lb)) return "HRR round count";
   // bra transforms
   if (ct.nbA)
     for (size_t q = 0; q < ct.baent.size(); ++q)
@@ -509,6 +590,49 @@ std::string check_class_tables(const ClassTables& ct) {
     for (size_t q = 0; q < ct.bbent.size(); ++q)
       if (ct.bbent[q].x < 0 || ct.bbent[q].x >= ct.ncB) return bad("bra B entry", (long long)q);
   return "";
+}
+
+// HRR holds exactly for moment integrals M(a, b) = int (x-A)^a (x-B)^b w(x) dx
+// of any weight w, since (x-B) = (x-A) + AB.  With the moments
+// mu_k = int (x-A)^k w = 1/(k+1) per axis, feed round 0 the values
+// (e 0| = prod_i mu_{e_i}, run the class's HRR rows on the host and compare
+// the top round with prod_i sum_j C(b_i, j) AB_i^(b_i-j) mu_{a_i+j}.
+double hrr_moment_error(const ClassTables& ct, const double AB[3]) {
+  auto mu = [](int k) { return 1.0 / (k + 1); };
+  std::vector<double> cur(ct.nkrow);
+  for (int r = 0; r < ct.nkrow; ++r)
+    cur[r] = mu(ct.erow_xyz[r].x) * mu(ct.erow_xyz[r].y) * mu(ct.erow_xyz[r].z);
+  const double c[13] = {1.0, AB[0], AB[1], AB[2], 2 * AB[0], 2 * AB[1], 2 * AB[2], AB[0] * AB[0], AB[1] * AB[1],
+                        AB[2] * AB[2], AB[0] * AB[1], AB[0] * AB[2], AB[1] * AB[2]};
+  for (int r = 1; r <= ct.nhrr; ++r) {
+    std::vector<double> nxt(ct.hrows[r], 0.0);
+    for (int i = ct.hstart[r]; i < ct.hstart[r + 1]; ++i) {
+      const uint4 h = ct.htab[i];
+      const unsigned nt = h.x >> 16, src[4] = {h.y & 0xFFFF, h.y >> 16, h.z & 0xFFFF, h.z >> 16};
+      double v = 0;
+      for (unsigned t = 0; t < nt; ++t) v += c[(h.w >> (4 * t)) & 0xF] * cur[src[t]];
+      nxt[h.x & 0xFFFF] = v;
+    }
+    cur.swap(nxt);
+  }
+  double worst = 0;
+  auto ca = cart(ct.la), cb = cart(ct.lb);
+  for (size_t ia = 0; ia < ca.size(); ++ia)
+    for (size_t ib = 0; ib < cb.size(); ++ib) {
+      double ref = 1.0, mag = 1.0;
+      for (int x = 0; x < 3; ++x) {
+        double s = 0, m = 0;
+        for (int j = 0; j <= cb[ib].v[x]; ++j) {
+          const double t = binom(cb[ib].v[x], j) * std::pow(AB[x], cb[ib].v[x] - j) * mu(ca[ia].v[x] + j);
+          s += t;
+          m += std::fabs(t);
+        }
+        ref *= s;
+        mag *= m;
+      }
+      worst = std::max(worst, std::fabs(cur[ia * cb.size() + ib] - ref) / mag);
+    }
+  return worst;
 }
 
 // ---------------------------------------------------------------------------
@@ -530,7 +654,7 @@ void buffer_sizes(const ClassTables& ct, int Kab, int Kc, int T, int G, int mode
   auto per_tg = [&](int n) -> long long { return mode == 0 ? (long long)n * G * Tp : (long long)T * G * n; };
   long long nK = (long long)ct.nkrow * ct.nC, nG = (long long)ct.nkrow * ct.ncc;
   int lb = ct.lb;
-  s.pair = (long long)Kab * kPairRec + 4;
+  s.pair = (long long)Kab * kPairRec + 16;  // + the tile's AB products
   s.aux = (long long)T * (3 + kAuxRec * Kc);
   s.loop = per_tg(ct.NV) + per_tg(ct.NW) + per_tg(ct.NF);
   s.P = per_t(ct.NACC);
@@ -538,11 +662,12 @@ void buffer_sizes(const ClassTables& ct, int Kab, int Kc, int T, int G, int mode
   // X holds the loop buffers, the gather output and odd HRR levels.
   long long Y = std::max(s.P, per_t((int)nK));
   long long X = std::max(s.loop, per_t((int)nG));
-  for (int j = 1; j <= lb; ++j) {
+  const int R = ct.nhrr;
+  for (int j = 1; j <= R; ++j) {
     long long sz = per_t(ct.hrows[j] * ct.nC);
     if (j & 1) X = std::max(X, sz); else Y = std::max(Y, sz);
   }
-  int cur = (lb & 1) ? 1 : 0;  // 0 = Y, 1 = X
+  int cur = (R & 1) ? 1 : 0;  // 0 = Y, 1 = X
   int baR = -1, bbR = -1;
   if (ct.nbA) { cur ^= 1; baR = cur; long long sz = per_t(ct.nbA * ct.nC); if (cur) X = std::max(X, sz); else Y = std::max(Y, sz); }
   if (ct.nbB) { cur ^= 1; bbR = cur; long long sz = per_t(ct.nbB * ct.nC); if (cur) X = std::max(X, sz); else Y = std::max(Y, sz); }
@@ -575,8 +700,8 @@ void buffer_sizes(const ClassTables& ct, int Kab, int Kc, int T, int G, int mode
   d->P = mk_t(ybase, ct.NACC);
   d->Gb = mk_t(xbase, (int)nG);
   d->H[0] = mk_t(ybase, (int)nK);
-  for (int j = 1; j <= lb; ++j) d->H[j] = mk_t((j & 1) ? xbase : ybase, ct.hrows[j] * ct.nC);
-  Buf last = d->H[lb];
+  for (int j = 1; j <= R; ++j) d->H[j] = mk_t((j & 1) ? xbase : ybase, ct.hrows[j] * ct.nC);
+  Buf last = d->H[R];
   if (ct.nbA) { d->BA = mk_t(baR ? xbase : ybase, ct.nbA * ct.nC); last = d->BA; }
   if (ct.nbB) { d->BB = mk_t(bbR ? xbase : ybase, ct.nbB * ct.nC); last = d->BB; }
   d->OUT = last;

@@ -104,3 +104,22 @@ def test_boys_device(lx):
     small = T < 117.0
     assert rel[small].max() < 3e-15, (rel[small].max(), T[small][np.unravel_index(rel[small].argmax(), rel[small].shape)[0]])
     assert rel[~small].max() < 6e-15, (rel[~small].max(), T[~small][np.unravel_index(rel[~small].argmax(), rel[~small].shape)[0]])
+
+
+HRR2 = [(la, lb, lc) for la in range(5) for lb in range(2, 5) for lc in (0, 2, 4, 6)]
+
+
+@pytest.mark.parametrize("la,lb,lc", HRR2)
+def test_class_two_quantum_hrr(lx, la, lb, lc):
+    """Classes with lb >= 2 through the two-quantum HRR rounds of Sec. 2.5.5
+    (both orientations hinted), against the oracle with the same criterion."""
+    p = W.class_problem(la, lb, lc, 5, 7, 2, 2, 1, box=6.0, exp_lo=0.1, exp_hi=50.0,
+                        seed=2000 + la * 100 + lb * 10 + lc)
+    for (a, b) in {(la, lb), (lb, la)}:
+        lx.hrr_hint(a, b, lc, 1)
+    try:
+        g = run(lx, p)
+    finally:
+        for (a, b) in {(la, lb), (lb, la)}:
+            lx.hrr_hint(a, b, lc, -1)
+    assert_parity(g, p)

@@ -79,6 +79,28 @@ def test_cholesky_reports_first_nonpositive_pivot(lx):
     assert info == 71
 
 
+def test_cholesky_drops_dependent_functions(lx):
+    """An aux basis holding one shell twice: the copy's pivots vanish, the
+    drop mode removes exactly its 2l+1 functions, and the solve still
+    satisfies V c = gamma (the copy's rows equal the original's)."""
+    cl = W.cluster((2, 1, 1), W.ORB_RECIPE_DFJ, W.AUX_RECIPE_DFJ, seed=503)
+    aux = cl.aux
+    dup = int(np.where(aux.l == 2)[0][0])
+    idx = list(range(aux.nshell)) + [dup]
+    aux2 = aux.subset(idx)
+    V = lx.MetricPlan(aux2).execute()
+    V0 = V.cpu().numpy()
+    _, info = lx.cholesky(V, drop_tol=1e-12)
+    assert info == 5
+    rng = np.random.default_rng(4)
+    g = rng.standard_normal(V0.shape[0])
+    aq = oracle.ao_offsets(aux2)
+    g[aq[-2]:aq[-1]] = g[aq[dup]:aq[dup + 1]]  # a consistent right-hand side
+    c = lx.cholesky_solve(V, torch.tensor(g, device="cuda")).cpu().numpy()
+    assert np.abs(c[aq[-2]:aq[-1]]).max() == 0.0
+    assert np.abs(V0 @ c - g).max() <= 1e-9 * np.abs(g).max()
+
+
 @pytest.mark.parametrize("n,nrhs", [(1, 1), (100, 1), (257, 3)])
 def test_cholesky_solve(lx, n, nrhs):
     A = spd(n, 100 + n)

@@ -227,8 +227,9 @@ def test_more_entry_points_reject_bad_arguments_on_host():
     assert L.lx3c_metric_plan(ctypes.byref(h), None, None) == -1
     assert L.lx3c_metric_execute(None, None, None) == -1
     assert L.lx3c_metric_info(None, None, 0) == -1
-    assert L.lx3c_cholesky(None, 4, 4, None, None) == -1
-    assert L.lx3c_cholesky(ctypes.c_void_p(256), 4, 3, None, None) == -1
+    assert L.lx3c_cholesky(None, 4, 4, 0.0, None, None) == -1
+    assert L.lx3c_cholesky(ctypes.c_void_p(256), 4, 3, 0.0, None, None) == -1
+    assert L.lx3c_cholesky(ctypes.c_void_p(256), 4, 4, 1.0, None, None) == -1
     assert L.lx3c_cholesky_solve(None, 4, 4, None, 1, None) == -1
     assert L.lx3c_dfj_coulomb(None, None, 0, None, None, None, None, None) == -1
     q = ctypes.c_double()
@@ -254,3 +255,19 @@ def test_class_tables_invariants_every_class():
             bad.append((la, lb, lc, pure, L.lx3c_last_error()))
     assert not bad, bad[:5]
     assert L.lx3c_class_tables_check(-1, 0, 0, 1) == -1
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_hrr_tables_exact_on_moment_integrals(variant):
+    """Both HRR variants (one or two quanta per round, Eq. hrr / Sec. 2.5.5)
+    reproduce moment integrals int (x-A)^a (x-B)^b w dx, for which HRR is
+    exact, for every bra class up to (hh|, and pass the table invariants."""
+    L = _lib.load()
+    AB = np.array([0.7, -1.3, 2.1])
+    e = ctypes.c_double()
+    for la in range(6):
+        for lb in range(6):
+            for lc in (0, 4):
+                assert L.lx3c_hrr_tables_check(la, lb, lc, 1, variant, AB.ctypes.data, ctypes.byref(e)) == 0, \
+                    L.lx3c_last_error()
+                assert e.value < 1e-14, (la, lb, lc, e.value)
