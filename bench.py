@@ -52,10 +52,11 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 
 # DRAM traffic of the (gg|i) K_ab=6 class per pair (512 ket shells, both oriented
 # launches), from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
-# on 64 pairs x 512 ket shells (59,150,592 + 208,663,552 bytes), scaled by pairs;
-# the integral blocks written are 4,312,448 bytes per pair, so traffic is 0.97x the
-# algorithmic bytes (no re-reads; the B-oriented launch reads back blocks it adds to).
-GGI_K6_DRAM_BYTES_PER_PAIR = (59150592 + 208663552) / 64
+# on 64 pairs x 512 ket shells (1,586,944 + 57,534,976 read, 111,942,400 +
+# 96,790,528 written), scaled by pairs; the integral blocks written are 4,312,448
+# bytes per pair, so traffic is 0.97x the algorithmic bytes (no re-reads; the
+# B-oriented launch reads back the blocks it adds to).
+GGI_K6_DRAM_BYTES_PER_PAIR = (1586944 + 57534976 + 111942400 + 96790528) / 64
 
 
 def parse():
