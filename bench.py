@@ -393,7 +393,8 @@ def extra_batch(dev):
                           per_class=round(fl / m0 / 1e6 / FP64_PEAK_GFLOPS, 4),
                           graph_persistent=round(fl / m1 / 1e6 / FP64_PEAK_GFLOPS, 4)),
                 launches=dict(per_class=int(info["plain_launches"]), graph_branches_kernel_nodes=int(info["branch_kernels"]),
-                              graph_persistent_kernel_nodes=int(info["graph_kernels"]), graph_launches=1),
+                              graph_persistent_kernel_nodes=int(info["graph_kernels"]),
+                              persistent_tiers=int(info["tiers"]), graph_launches=1),
                 speedup_graph_vs_per_class=round(m0 / m2, 4))
 
 

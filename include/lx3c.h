@@ -418,21 +418,24 @@ lx3c_status lx3c_dfj_coulomb(lx3c_dfj* plan, const double* L, int64_t lda, const
  *   c[m] naux_ao in; gamma[m], J[m] out; all owned by the caller and kept
  *   alive while the batch is executed), orders the class launches longest
  *   first and captures two CUDA graphs of the whole build (zeroing,
- *   precompute, integrals, J symmetrisation): graph 1 runs every
- *   (class launch, tile) work item in ONE persistent kernel that pulls items
- *   from an atomic counter (no CTA waits on another); graph 2 runs the class
- *   launches themselves on four parallel graph branches.  Setup; may
+ *   precompute, integrals, J finish): graph 1 runs every (class launch,
+ *   tile) work item in persistent kernels, one per shared-memory tier (the
+ *   items that fit two CTAs per SM, then the rest), each sized for its
+ *   tier's largest item and pulling items longest first from its own atomic
+ *   counter (no CTA waits on another); graph 2 runs the class launches
+ *   themselves on four parallel graph branches.  Setup; may
  *   synchronise.  Returns LX3C_ECUDA if a capture fails.
  * lx3c_batch_execute: mode 1 or 2 launches graph 1 or 2 (one
  *   cudaGraphLaunch on `stream`); mode 0 runs the same tasks as per-class
  *   launches (lx3c_dfj_execute per molecule), for comparison; any other mode
  *   is LX3C_EINVAL.  Asynchronous.
- * lx3c_batch_info: out[0..13] = molecules, screened triples, integrals,
+ * lx3c_batch_info: out[0..15] = molecules, screened triples, integrals,
  *   algorithmic flops, plain kernel launches, persistent-graph kernel nodes,
  *   work items, class launches merged, persistent smem bytes, persistent
  *   grid, tuned signatures, signatures measured by this plan, branch-graph
  *   kernel nodes, branches, tile slots (tiles x triples per tile, summed
- *   over launches; screened triples / slots is the tile fill).
+ *   over launches; screened triples / slots is the tile fill), persistent
+ *   tiers.  (out[0..15].)
  */
 lx3c_status lx3c_batch_plan(lx3c_batch** out, int nmol, const lx3c_basis* const* orbs,
                             const lx3c_basis* const* auxs, double schwarz_tol, const char* tune_cache,

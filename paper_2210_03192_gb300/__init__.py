@@ -373,7 +373,7 @@ class Batch:
     graph, class launches on parallel branches) or 0 (per-class launches)."""
 
     INFO = ["molecules", "tasks", "integrals", "flops", "plain_launches", "graph_kernels", "work_items",
-            "class_launches", "smem", "grid", "tuned", "measured", "branch_kernels", "branches", "slots"]
+            "class_launches", "smem", "grid", "tuned", "measured", "branch_kernels", "branches", "slots", "tiers"]
 
     def __init__(self, mols, schwarz_tol=1e-12, tune_cache=None, stream=None):
         L = _lib.load()

@@ -806,12 +806,20 @@ struct lx3c_batch {
   // bound state
   ClassDesc* d_descs = nullptr;
   int2* d_work = nullptr;
-  unsigned long long* d_counter = nullptr;
+  unsigned long long* d_counter = nullptr;  // one per tier
   long long nwork = 0;
   int ndesc = 0;
   int smem = 0;
   int grid = 0;
-  cudaGraph_t graph = nullptr;        // mode 1: one persistent kernel
+  // mode 1 splits the work items into shared-memory tiers, each run by a
+  // persistent kernel sized for the tier's largest item: items that fit two
+  // CTAs per SM, then the rest (one CTA per SM)
+  struct Tier {
+    long long off = 0, n = 0;
+    int smem = 0, grid = 0;
+  };
+  std::vector<Tier> tiers;
+  cudaGraph_t graph = nullptr;        // mode 1: persistent kernels, one per tier
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph2 = nullptr;       // mode 2: class launches on parallel branches
   cudaGraphExec_t exec2 = nullptr;
@@ -1059,12 +1067,28 @@ lx3c_status lx3c_batch_bind(lx3c_batch* b, const double* const* D, const double*
     }
   }
   std::stable_sort(order.begin(), order.end(), [](auto& x, auto& y) { return x.first > y.first; });
+  // tiers: the items whose shared memory lets the persistent kernel keep two
+  // CTAs per SM, then the others; longest first within each tier
   std::vector<int2> work;
-  for (auto& o : order)
-    for (long long t = 0; t < descs[o.second].ntiles; ++t) work.push_back(int2{o.second, (int)t});
+  b->tiers.clear();
+  for (int tier = 0; tier < 2; ++tier) {
+    lx3c_batch::Tier T;
+    T.off = (long long)work.size();
+    for (auto& o : order) {
+      const int sm = descs[o.second].smem_doubles * 8;
+      const bool two = persistent_occupancy(sm) >= 2;
+      if ((tier == 0) != two) continue;
+      T.smem = std::max(T.smem, sm);
+      for (long long t = 0; t < descs[o.second].ntiles; ++t) work.push_back(int2{o.second, (int)t});
+    }
+    T.n = (long long)work.size() - T.off;
+    if (!T.n) continue;
+    T.grid = dev_nsm(b->ds) * persistent_occupancy(T.smem);
+    b->tiers.push_back(T);
+  }
   cudaFree(b->d_descs);
   cudaFree(b->d_work);
-  if (!b->d_counter) DCUDA(cudaMalloc(&b->d_counter, sizeof(unsigned long long)));
+  if (!b->d_counter) DCUDA(cudaMalloc(&b->d_counter, 2 * sizeof(unsigned long long)));
   DCUDA(cudaMalloc(&b->d_descs, descs.size() * sizeof(ClassDesc)));
   DCUDA(cudaMalloc(&b->d_work, std::max<size_t>(work.size(), 1) * sizeof(int2)));
   DCUDA(cudaMemcpy(b->d_descs, descs.data(), descs.size() * sizeof(ClassDesc), cudaMemcpyHostToDevice));
@@ -1072,7 +1096,7 @@ lx3c_status lx3c_batch_bind(lx3c_batch* b, const double* const* D, const double*
   b->nwork = (long long)work.size();
   b->ndesc = (int)descs.size();
   b->smem = smem;
-  b->grid = dev_nsm(b->ds) * persistent_occupancy(smem);
+  b->grid = b->tiers.empty() ? 0 : b->tiers[0].grid;
   // capture the whole batched build in one graph
   if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -1091,9 +1115,12 @@ lx3c_status lx3c_batch_bind(lx3c_batch* b, const double* const* D, const double*
       b->graph_kernels += 2;
     }
   }
-  cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), cap);
-  launch_persistent(b->d_descs, b->d_work, b->nwork, b->d_counter, b->grid, b->smem, cap);
-  b->graph_kernels += 1;
+  for (size_t t = 0; t < b->tiers.size(); ++t) {
+    const auto& T = b->tiers[t];
+    cudaMemsetAsync(b->d_counter + t, 0, sizeof(unsigned long long), cap);
+    launch_persistent(b->d_descs, b->d_work + T.off, T.n, b->d_counter + t, T.grid, T.smem, cap);
+    b->graph_kernels += 1;
+  }
   for (int m = 0; m < nmol; ++m) {
     launch_fix_finish(b->mols[m]->d_gacc, b->mols[m]->naux_ao, gamma[m], cap);
     launch_fix_finish_J(b->mols[m]->d_Jacc, b->mols[m]->nao, J[m], cap);
@@ -1139,8 +1166,8 @@ lx3c_status lx3c_batch_info(const lx3c_batch* b, double* out, int n) {
   const double v[] = {(double)b->mols.size(), tasks, nint, flops, (double)b->plain_launches,
                       (double)b->graph_kernels, (double)b->nwork, (double)b->ndesc, (double)b->smem,
                       (double)b->grid, (double)b->tuned.size(), (double)b->ntuned_measured,
-                      (double)b->branch_kernels, (double)kBranches, slots};
-  for (int i = 0; i < n && i < 15; ++i) out[i] = v[i];
+                      (double)b->branch_kernels, (double)kBranches, slots, (double)b->tiers.size()};
+  for (int i = 0; i < n && i < 16; ++i) out[i] = v[i];
   return LX3C_OK;
 }
 

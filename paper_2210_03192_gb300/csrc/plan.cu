@@ -360,6 +360,24 @@ ClassTables build(int la, int lb, int lc, int bra_pure, int hrr2) {
     ct.acc_key.push_back(int4{cart_index(e.v[0], e.v[1], e.v[2]) | (e.l() << 16), k,
                               cart_index(n.v[0], n.v[1], n.v[2]) | ((lc - k) << 16), 0});
   }
+  {
+    // keep only the weights some accumulator reads (for la + lb < lc the
+    // targets reach k <= la + lb only) and renumber them densely
+    std::vector<int> remap(ct.NW, -1);
+    for (unsigned a : ct.atab) remap[a >> 16] = 0;
+    std::vector<int4> kept;
+    for (const int4& it : ct.wtab) {
+      const int dst = it.x & 0xFFFF;
+      if (remap[dst] < 0) continue;
+      remap[dst] = (int)kept.size();
+      int4 k2 = it;
+      k2.x = (it.x & ~0xFFFF) | remap[dst];
+      kept.push_back(k2);
+    }
+    for (unsigned& a : ct.atab) a = (a & 0xFFFF) | ((unsigned)remap[a >> 16] << 16);
+    ct.wtab = kept;
+    ct.NW = (int)kept.size();
+  }
   // gather CSR by target id = row*ncc + c, items sorted by descending term count
   int ngt = ct.nkrow * ct.ncc;
   ct.gptr.assign(ngt + 1, 0);

@@ -57,7 +57,7 @@ def test_batch_graph_equals_plain_and_oracle(lx):
         for g, J in ((g1[m], J1[m]), (g2[m], J2[m])):
             assert np.array_equal(g, g0[m].cpu().numpy())
             assert np.array_equal(J, J0[m].cpu().numpy())
-    assert info["branch_kernels"] == info["graph_kernels"] - 1 + info["class_launches"]
+    assert info["branch_kernels"] == info["graph_kernels"] - info["tiers"] + info["class_launches"]
     # oracle on the smallest molecule, same screened tasks
     cl = mols[0]
     plan = lx.DFJPlan(cl.orb, cl.aux, 1e-12)
