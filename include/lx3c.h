@@ -55,6 +55,10 @@ typedef int lx3c_status;
 #define LX3C_LMAX_AUX 6
 #define LX3C_KMAX 16
 
+/* lx3c_dfj_plan flags */
+#define LX3C_DFJ_GRADIENT 1
+#define LX3C_DFJ_CONTRACT 2
+
 typedef struct lx3c_basis lx3c_basis;
 typedef struct lx3c_plan lx3c_plan;
 typedef struct lx3c_dfj lx3c_dfj;
@@ -253,8 +257,18 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  * shell order, components m = -l..l), for every ket shell P of the aux basis.
  *
  * lx3c_dfj_plan: setup (synchronises `stream`, not part of the timed path).
- *   flags bit 0: also prepare the nuclear gradient (lx3c_dfj_grad); needs an
- *   atom index on every shell and orbital shells with l < LX3C_LMAX_ORB.
+ *   flags LX3C_DFJ_GRADIENT (bit 0): also prepare the nuclear gradient
+ *   (lx3c_dfj_grad); needs an atom index on every shell and orbital shells
+ *   with l < LX3C_LMAX_ORB.
+ *   flags LX3C_DFJ_CONTRACT (bit 1): digest at the (e 0|c) level, the DF-J
+ *   analogue of the J-engine the paper names as the follow-up (Sec. 4: the
+ *   density is contracted with integral intermediates rather than with the
+ *   integrals): per pair launch the bra map M (the HRR and bra transforms,
+ *   (AB|C) = sum_e M[AB][e] (e 0|C)) is formed once per pair; per triple
+ *   gamma_P = sum_c T_Cc sum_e (M^T D)_e (e 0|c) and y_e += sum_c (e 0|c)
+ *   (T^T c_P)_c, then J_AB += M y per pair -- no ket transform, HRR or bra
+ *   transform per triple.  Launches whose bra map does not fit in shared
+ *   memory keep the per-integral digestion.  Same results to rounding.
  *   Screening: a (pair, ket) triple is kept when Q_ab Q_P >= schwarz_tol, with
  *   Q_ab = 20 sum over primitive pairs of |c_a c_b| exp(-za zb/g AB^2)
  *   sqrt(2 pi^{5/2}/(g^2 sqrt(2g))) (|PA|^2+1/(2g))^{la/2} (|PB|^2+1/(2g))^{lb/2}

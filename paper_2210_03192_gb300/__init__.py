@@ -148,13 +148,16 @@ def eri3c_host(orb, aux, pairs, auxs, bra_pure=True, out=None, stream=None):
 class DFJPlan:
     """Screened DF-J build (lx3c_dfj): gamma_P and J_mn from D and c, Sec. 3."""
 
-    def __init__(self, orb, aux, schwarz_tol=1e-12, gradient=False, stream=None):
+    def __init__(self, orb, aux, schwarz_tol=1e-12, gradient=False, contract=False, stream=None):
+        """contract: digest at the (e 0|c) level (LX3C_DFJ_CONTRACT), the DF-J
+        analogue of a J-engine: no ket transform, HRR or bra transform per triple."""
         L = _lib.load()
         self.orb = orb if isinstance(orb, DeviceBasis) else DeviceBasis(orb, stream)
         self.aux = aux if isinstance(aux, DeviceBasis) else DeviceBasis(aux, stream)
         self.handle = ctypes.c_void_p()
+        flags = (1 if gradient else 0) | (2 if contract else 0)
         check(L.lx3c_dfj_plan(ctypes.byref(self.handle), self.orb.handle, self.aux.handle, float(schwarz_tol),
-                              1 if gradient else 0, _stream_handle(stream)), "lx3c_dfj_plan")
+                              flags, _stream_handle(stream)), "lx3c_dfj_plan")
         info = np.zeros(11)
         check(L.lx3c_dfj_info(self.handle, ptr(info), 11), "lx3c_dfj_info")
         self.ngroups, self.ntasks, self.nint, self.flops, self.launches, self.nao, self.naux_ao = (

@@ -106,7 +106,7 @@ lx3c_status device_class(DevState* s, const ClassTables& ct, DevClass** out) {
     *out = &it->second;
     return LX3C_OK;
   }
-  size_t offs[16];
+  size_t offs[18];
   std::vector<char> blob = class_blob(ct, offs);
   DevClass dc;
   CUDA_TRY(cudaMalloc(&dc.blob, blob.size()));
@@ -138,18 +138,18 @@ size_t append(std::vector<char>& blob, const std::vector<T>& v) {
 }
 }  // namespace
 
-std::vector<char> class_blob(const ClassTables& ct, size_t f[16]) {
+std::vector<char> class_blob(const ClassTables& ct, size_t f[18]) {
   std::vector<char> blob;
   f[0] = append(blob, ct.vtab); f[1] = append(blob, ct.wtab); f[2] = append(blob, ct.atab);
   f[3] = append(blob, ct.gptr); f[4] = append(blob, ct.gterm); f[5] = append(blob, ct.gdst);
   f[6] = append(blob, ct.pal); f[7] = append(blob, ct.kptr); f[8] = append(blob, ct.kent);
   f[9] = append(blob, ct.htab); f[10] = append(blob, ct.baptr); f[11] = append(blob, ct.baent);
   f[12] = append(blob, ct.bbptr); f[13] = append(blob, ct.bbent); f[14] = append(blob, ct.gell);
-  f[15] = append(blob, ct.gslice);
+  f[15] = append(blob, ct.gslice); f[16] = append(blob, ct.ktptr); f[17] = append(blob, ct.ktent);
   return blob;
 }
 
-void class_blob_pointers(DevClass& dc, const void* dev_blob, const size_t f[16]) {
+void class_blob_pointers(DevClass& dc, const void* dev_blob, const size_t f[18]) {
   const char* b = (const char*)dev_blob;
   dc.vtab = (const uint4*)(b + f[0]);
   dc.wtab = (const int4*)(b + f[1]);
@@ -167,6 +167,8 @@ void class_blob_pointers(DevClass& dc, const void* dev_blob, const size_t f[16])
   dc.bbent = (const int2*)(b + f[13]);
   dc.gell = (const unsigned*)(b + f[14]);
   dc.gslice = (const int2*)(b + f[15]);
+  dc.ktptr = (const int*)(b + f[16]);
+  dc.ktent = (const int2*)(b + f[17]);
 }
 
 void fill_desc_common(ClassDesc& d, const ClassTables& ct, const DevClass& dc, const double* boys_tab,
@@ -192,6 +194,7 @@ void fill_desc_common(ClassDesc& d, const ClassTables& ct, const DevClass& dc, c
   d.nbA = ct.nbA; d.nbB = ct.nbB;
   d.vtab = dc.vtab; d.wtab = dc.wtab; d.atab = dc.atab; d.gptr = dc.gptr; d.gterm = dc.gterm;
   d.gdst = dc.gdst; d.pal = dc.pal; d.kptr = dc.kptr; d.kent = dc.kent; d.htab = dc.htab;
+  d.ktptr = dc.ktptr; d.ktent = dc.ktent;
   d.gell = dc.gell; d.gslice = dc.gslice;
   d.baptr = dc.baptr; d.baent = dc.baent; d.bbptr = dc.bbptr; d.bbent = dc.bbent;
   d.boys_tab = boys_tab; d.boys_mid = boys_mid; d.boys_cL = boys_large_const(d.L);

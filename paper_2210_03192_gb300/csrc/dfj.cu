@@ -41,6 +41,8 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st);
 int eri3c_occupancy(int smem_bytes);
 cudaError_t launch_persistent(const ClassDesc* descs, const int2* work, long long nwork, unsigned long long* counter,
                               int grid, int smem_bytes, cudaStream_t st);
+cudaError_t launch_jeng_matrix(const ClassDesc& d, int grid, cudaStream_t st);
+cudaError_t launch_jeng_pair(const ClassDesc& d, int finish, cudaStream_t st);
 int persistent_occupancy(int smem_bytes);
 }  // namespace lx3c
 
@@ -181,6 +183,12 @@ constexpr double kSchwarzSafety = 20.0;
 struct DfjLaunch {
   ClassDesc desc;
   int grid = 1;
+  // contraction at the (e 0|c) level (flag LX3C_DFJ_CONTRACT): the digest-5
+  // descriptor, the bra-map pass (one sub-pair per tile, nC = nkrow) and its grid
+  bool jeng = false;
+  ClassDesc jdesc, mdesc;
+  int mgrid = 1;
+  double jflops = 0, pflops = 0;
   long long ntiles = 0;
   int4* d_sub = nullptr;
   int* d_prim = nullptr;
@@ -272,6 +280,12 @@ struct lx3c_dfj {
   unsigned long long* d_gacc = nullptr;
   unsigned long long* d_Jacc = nullptr;
   unsigned long long* d_facc = nullptr;
+  // (e 0|c)-level contraction: bra maps, D through M^T and y, sized for the
+  // largest launch and reused launch after launch
+  bool contract = false;
+  double* d_jM = nullptr;
+  double* d_jD = nullptr;
+  unsigned long long* d_jY = nullptr;
 };
 
 namespace lx3c {
@@ -300,6 +314,9 @@ void lx3c_dfj_destroy(lx3c_dfj* p) {
   cudaFree(p->d_gacc);
   cudaFree(p->d_Jacc);
   cudaFree(p->d_facc);
+  cudaFree(p->d_jM);
+  cudaFree(p->d_jD);
+  cudaFree(p->d_jY);
   delete p;
 }
 
@@ -311,6 +328,7 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
   if (orb->nshell <= 0 || aux->nshell <= 0) return dfail(LX3C_EINVAL, "empty basis");
   if (!(schwarz_tol >= 0.0)) return dfail(LX3C_EINVAL, "negative or NaN tolerance");
   const bool want_grad = (flags & 1) != 0;
+  const bool contract = (flags & 2) != 0;
   for (int64_t s = 0; s < orb->nshell; ++s)
     if (orb->l[s] > LX3C_LMAX_ORB - (want_grad ? 1 : 0))
       return dfail(LX3C_ENOTSUP, "orbital shell beyond the supported l");
@@ -465,6 +483,42 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
       d.aux_ao = g.d_aux_ao;
       const int occ = eri3c_occupancy(d.smem_doubles * 8);
       L.grid = (int)std::min<long long>(L.ntiles, (long long)dev_nsm(ds) * occ * 8);
+      if (contract) {
+        // the bra-map pass: the class stages with nC = nkrow, one sub-pair per tile
+        ClassTables ctm = *ct;
+        ctm.nC = ct->nkrow;
+        ctm.NV = ctm.NW = ctm.NF = ctm.NACC = 0;
+        ctm.ncc = 0;
+        LaunchShape shm{1, 1, 1, 0};
+        ClassDesc dm;
+        fill_desc_common(dm, ctm, *dc, dev_boys_tab(ds), dev_boys_mid(ds), o, kmax[o], Kab, g.Kc, shm);
+        ClassDesc dj = d;
+        dj.digest = 5;
+        dj.dscr = place_epilogue_scratch(dj, ct->nkrow + 2LL * dj.T * ct->ncc);
+        if ((long long)dm.smem_doubles * 8 <= 232448 && (long long)dj.smem_doubles * 8 <= 232448) {
+          dm.npair = np; dm.naux = na; dm.nsub = d.nsub; dm.subpairs = d.subpairs; dm.pairab = g.d_pairab;
+          L.jeng = true;
+          L.mdesc = dm;
+          L.jdesc = dj;
+          L.mgrid = (int)std::min<long long>(d.nsub, (long long)dev_nsm(ds) * 4);
+          // flops: per triple the primitive loop, the gather and the two
+          // contractions over (e, c) (plus gamma's ket transform); per sub-pair
+          // the bra map (the HRR and bra stages at nC = nkrow) and two GEMVs
+          const double gather = 2.0 * ct->gterm.size(), ket = 2.0 * ct->kent.size() * ct->nkrow;
+          const double hrrbra = (ct->flops_contr - gather - ket) / ct->nC * ct->nkrow;
+          const double nab = (double)d.onA * d.onB, nk = ct->nkrow;
+          double tris = 0, primtris = 0;
+          for (auto& sp : sub[o]) {
+            tris += g.counts[sp.x];
+            primtris += (double)g.counts[sp.x] * sp.z * g.Kc;
+          }
+          L.jflops = primtris * ct->flops_prim + tris * (gather + 4.0 * nk * ct->ncc + 2.0 * ct->kent.size()) +
+                     (double)d.nsub * (hrrbra + 4.0 * nab * nk);
+          // the same triples digested per integral (what the plain path counts)
+          L.pflops = primtris * ct->flops_prim + tris * (ct->flops_contr + 4.0 * nab * ct->nC);
+          p->contract = true;
+        }
+      }
     }
     if (!want_grad) continue;
     // ---- gradient launches
@@ -575,6 +629,27 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
           L.desc.Tb = p->d_sph + p->sph_off[g.lb];
         }
   }
+  if (p->contract) {
+    size_t nm = 1, nd = 1;
+    for (auto& g : p->groups)
+      for (auto& L : g.L)
+        if (L.jeng) {
+          nm = std::max(nm, (size_t)L.desc.nsub * L.desc.onA * L.desc.onB * L.mdesc.nkrow);
+          nd = std::max(nd, (size_t)L.desc.nsub * L.mdesc.nkrow);
+        }
+    DCUDA(cudaMalloc(&p->d_jM, nm * 8));
+    DCUDA(cudaMalloc(&p->d_jD, nd * 8));
+    DCUDA(cudaMalloc(&p->d_jY, nd * 16));
+    for (auto& g : p->groups)
+      for (auto& L : g.L)
+        if (L.jeng) {
+          for (ClassDesc* d : {&L.mdesc, &L.jdesc}) {
+            d->jM = p->d_jM;
+            d->jD = p->d_jD;
+            d->jY = p->d_jY;
+          }
+        }
+  }
   DCUDA(cudaMalloc(&p->d_gacc, (size_t)p->naux_ao * 16));
   DCUDA(cudaMalloc(&p->d_Jacc, (size_t)p->nao * p->nao * 16));
   if (want_grad) DCUDA(cudaMalloc(&p->d_facc, (size_t)p->natom * 3 * 16));
@@ -595,12 +670,27 @@ lx3c_status lx3c_dfj_execute(lx3c_dfj* p, const double* D, const double* c, doub
     DCUDA(launch_aux_precompute(p->aux->dev(), g.d_auxs, na, g.Kc, g.d_auxrec, g.d_auxc, st));
     for (auto& L : g.L) {
       if (!L.ntiles) continue;
-      ClassDesc d = L.desc;
+      ClassDesc d = L.jeng ? L.jdesc : L.desc;
       d.D = D;
       d.cvec = c;
       d.gacc = gamma ? p->d_gacc : nullptr;
       d.Jacc = J ? p->d_Jacc : nullptr;
-      DCUDA(launch_eri3c(d, L.grid, st));
+      if (L.jeng) {
+        // bra maps, D through M^T, the tiles at the (e 0|c) level, then J = M y
+        ClassDesc dm = L.mdesc;
+        dm.D = D;
+        dm.gacc = d.gacc;
+        dm.Jacc = d.Jacc;
+        dm.ldD = d.ldD;
+        dm.pair_ao = d.pair_ao;
+        if (J) DCUDA(cudaMemsetAsync(p->d_jY, 0, (size_t)d.nsub * d.nkrow * 16, st));
+        DCUDA(launch_jeng_matrix(dm, L.mgrid, st));
+        if (gamma) DCUDA(launch_jeng_pair(dm, 0, st));
+        DCUDA(launch_eri3c(d, L.grid, st));
+        if (J) DCUDA(launch_jeng_pair(dm, 1, st));
+      } else {
+        DCUDA(launch_eri3c(d, L.grid, st));
+      }
     }
   }
   if (gamma) DCUDA(launch_fix_finish(p->d_gacc, p->naux_ao, gamma, st));
@@ -711,7 +801,13 @@ lx3c_status lx3c_dfj_info(const lx3c_dfj* p, double* out, int n) {
   if (!p || (!out && n > 0)) return dfail(LX3C_EINVAL, "null pointer");
   double tasks = 0, nint = 0, flops = 0, launches = 2, gflops = 0, glaunches = p->gradient ? 1 : 0, slots = 0;
   for (auto& g : p->groups) {
-    for (auto& L : g.L) slots += (double)L.ntiles * L.desc.T;
+    for (auto& L : g.L) {
+      slots += (double)L.ntiles * L.desc.T;
+      if (L.jeng) {
+        flops += L.jflops - L.pflops;
+        launches += 3;  // bra maps, D through M^T, J = M y
+      }
+    }
     tasks += (double)g.ntasks;
     nint += g.nint;
     flops += g.flops;

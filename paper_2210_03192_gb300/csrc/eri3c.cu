@@ -244,21 +244,21 @@ __device__ __forceinline__ void dec3(unsigned w, int mode, const FDiv& fT, const
 
 // Segmented dot products out[o] += sum_{r < len} prod(o, r) for o < nout,
 // each partial result handed to emit(o, value), which adds it to global
-// memory with an atomic.  The FP64 pipe charges a whole warp instruction
+// memory with an atomic (whole: one lane per output, each emitted once).  The FP64 pipe charges a whole warp instruction
 // whatever the number of active lanes, and one lane's dependent FMAs are
 // serialised, so the mapping follows the estimated chain length: one lane per
 // output (two partial sums) when there are many outputs, else one warp per
 // (output, 128-term chunk) whose lanes each emit their own partial sum (a warp
 // shuffle reduction here costs the whole kernel registers).
 template <class Prod, class Emit>
-__device__ __forceinline__ void seg_dot(int nout, int len, const Prod& prod, const Emit& emit) {
+__device__ __forceinline__ void seg_dot(int nout, int len, const Prod& prod, const Emit& emit, bool whole = false) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int kWarps = kThreads / 32, kChunk = 128;
   if (nout <= 0 || len <= 0) return;
   const int nch = (len + kChunk - 1) / kChunk;
   const long long lane_steps = (long long)((nout + kThreads - 1) / kThreads) * ((len + 1) / 2);
   const long long warp_steps = (long long)((nout * nch + kWarps - 1) / kWarps) * ((min(len, kChunk) + 31) / 32 + 1);
-  if (lane_steps <= warp_steps) {
+  if (whole || lane_steps <= warp_steps) {
     for (int o = tid; o < nout; o += kThreads) {
       double s0 = 0.0, s1 = 0.0;
       int r = 0;
@@ -280,11 +280,122 @@ __device__ __forceinline__ void seg_dot(int nout, int len, const Prod& prod, con
   }
 }
 
+// HRR rounds (Eq. hrr; Sec. 2.5.5 for two-quantum rounds) and the optional
+// solid-harmonic bra transforms on tv triples of H[0]; returns the buffer
+// holding the final block.
+__device__ __forceinline__ Buf hrr_and_bra(const ClassDesc& d, double* sm, int T, int tv, int mode, const FDiv& fT) {
+  const unsigned tid = threadIdx.x;
+  // ---- HRR (Eq. hrr) round by round: each row is dst = sum_t coef_t src_t
+  // over 2 terms (one quantum moved, Eq. hrr) or 3-4 terms (two quanta,
+  // Sec. 2.5.5), the coefficients products of AB components
+  for (int j = 1; j <= d.nhrr; ++j) {
+    FDiv fX, fC;
+    const int nx = d.hrows[j] * d.nC;
+    fX.init(nx);
+    fC.init(d.nC);
+    const unsigned n = (unsigned)(T * nx);
+    const Buf hi = d.H[j - 1], ho = d.H[j];
+    const double* abp = sm + d.ab_base;
+    for (unsigned w = tid; w < n; w += kThreads) {
+      int t, x;
+      dec2(w, mode, fT, fX, t, x);
+      if (t >= tv) continue;
+      const int r = (int)fC.div(x), C = x - r * d.nC;
+      const uint4 e = __ldg(d.htab + d.hstart[j] + r);
+      const unsigned nt = e.x >> 16;
+      double v = fma(abp[(e.w >> 4) & 0xF], sm[BUF_T(hi, (int)(e.y >> 16) * d.nC + C, t)],
+                     sm[BUF_T(hi, (int)(e.y & 0xFFFF) * d.nC + C, t)]);
+      if (nt > 2) v = fma(abp[(e.w >> 8) & 0xF], sm[BUF_T(hi, (int)(e.z & 0xFFFF) * d.nC + C, t)], v);
+      if (nt > 3) v = fma(abp[(e.w >> 12) & 0xF], sm[BUF_T(hi, (int)(e.z >> 16) * d.nC + C, t)], v);
+      sm[BUF_T(ho, (int)(e.x & 0xFFFF) * d.nC + C, t)] = v;
+    }
+    __syncthreads();
+  }
+  // ---- optional solid-harmonic bra
+  Buf cur = d.H[d.nhrr];
+  if (d.nbA) {
+    FDiv fX, fC, fB;
+    const int nx = d.nbA * d.nC;
+    fX.init(nx);
+    fC.init(d.nC);
+    fB.init(d.ncB);
+    const unsigned n = (unsigned)(T * nx);
+    for (unsigned w = tid; w < n; w += kThreads) {
+      int t, x;
+      dec2(w, mode, fT, fX, t, x);
+      if (t >= tv) continue;
+      const int row = (int)fC.div(x), C = x - row * d.nC;
+      const int A = (int)fB.div(row), ib = row - A * d.ncB;
+      const int q0 = __ldg(d.baptr + A), q1 = __ldg(d.baptr + A + 1);
+      double s;
+      const int2 e0 = __ldg(d.baent + q0);
+      if (q1 - q0 == 1 && e0.y == 0) {
+        s = sm[BUF_T(cur, (e0.x * d.ncB + ib) * d.nC + C, t)];
+      } else {
+        s = 0.0;
+        for (int q = q0; q < q1; ++q) {
+          const int2 e = __ldg(d.baent + q);
+          s = fma(__ldg(d.pal + e.y), sm[BUF_T(cur, (e.x * d.ncB + ib) * d.nC + C, t)], s);
+        }
+      }
+      sm[BUF_T(d.BA, x, t)] = s;
+    }
+    __syncthreads();
+    cur = d.BA;
+  }
+  if (d.nbB) {
+    // items B-slowest in mode 1: a warp's lanes share B's trip count
+    FDiv fX, fC, fB, fAC;
+    const int nx = d.nbB * d.nC;
+    const int nBs = d.nB, nAC = (d.nbB / d.nB) * d.nC;
+    fX.init(nx);
+    fC.init(d.nC);
+    fB.init(nBs);
+    fAC.init(nAC);
+    const unsigned n = (unsigned)(T * nx);
+    for (unsigned w = tid; w < n; w += kThreads) {
+      int t, x;
+      dec2(w, mode, fT, fX, t, x);
+      if (t >= tv) continue;
+      int A, B, C;
+      if (mode == 0) {
+        const int row = (int)fC.div(x);
+        C = x - row * d.nC;
+        A = (int)fB.div(row);
+        B = row - A * nBs;
+      } else {
+        B = (int)fAC.div(x);
+        const int rem = x - B * nAC;
+        A = (int)fC.div(rem);
+        C = rem - A * d.nC;
+      }
+      x = (A * nBs + B) * d.nC + C;
+      const int q0 = __ldg(d.bbptr + B), q1 = __ldg(d.bbptr + B + 1);
+      double s;
+      const int2 e0 = __ldg(d.bbent + q0);
+      if (q1 - q0 == 1 && e0.y == 0) {
+        s = sm[BUF_T(cur, (A * d.ncB + e0.x) * d.nC + C, t)];
+      } else {
+        s = 0.0;
+        for (int q = q0; q < q1; ++q) {
+          const int2 e = __ldg(d.bbent + q);
+          s = fma(__ldg(d.pal + e.y), sm[BUF_T(cur, (A * d.ncB + e.x) * d.nC + C, t)], s);
+        }
+      }
+      sm[BUF_T(d.BB, x, t)] = s;
+    }
+    __syncthreads();
+    cur = d.BB;
+  }
+  return cur;
+}
+
 // One tile: (sub-pair, up to T ket shells) through every stage, ending in the
 // store, the DF-J digestion or the gradient digestion.  kMulti instantiates
-// the several-density digestion on tensor-core tiles (digest == 4) in a
-// kernel of its own, so that the other launches keep the lower register
-// count of the plain instantiation.
+// the several-density digestion on tensor-core tiles (digest == 4) and the
+// contraction at the (e 0|c) level (digest == 5) in a kernel of its own, so
+// that the other launches keep the lower register count of the plain
+// instantiation.
 template <bool kMulti>
 __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, double* sm) {
   const unsigned tid = threadIdx.x;
@@ -331,11 +442,12 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
         // the HRR coefficients: 1, AB_i, 2 AB_i, AB_i^2, AB_x AB_y, AB_x AB_z, AB_y AB_z
         const double sg = d.orient ? -1.0 : 1.0;
         const double x = sg * d.pairab[pair * 3], y = sg * d.pairab[pair * 3 + 1], z = sg * d.pairab[pair * 3 + 2];
-        const double ab[3] = {x, y, z};
+        const int ax = tid >= 1 && tid <= 9 ? (int)(tid - 1) % 3 : 0;
+        const double u = ax == 0 ? x : (ax == 1 ? y : z);
         double v = 1.0;
-        if (tid >= 1 && tid <= 3) v = ab[tid - 1];
-        else if (tid >= 4 && tid <= 6) v = 2.0 * ab[tid - 4];
-        else if (tid >= 7 && tid <= 9) v = ab[tid - 7] * ab[tid - 7];
+        if (tid >= 1 && tid <= 3) v = u;
+        else if (tid >= 4 && tid <= 6) v = 2.0 * u;
+        else if (tid >= 7 && tid <= 9) v = u * u;
         else if (tid == 10) v = x * y;
         else if (tid == 11) v = x * z;
         else if (tid == 12) v = y * z;
@@ -546,6 +658,65 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       }
     }
     __syncthreads();
+    if (kMulti && d.digest == 5) {
+      // ---- DF-J contracted at the (e 0|c) level (the analogue of a
+      // J-engine: D and c meet the intermediates, not the integrals).  With
+      // the pair's bra map M (HRR then bra transforms, (AB|C) = sum_e
+      // M[AB][e] (e 0|C)) and the ket transform T, (e 0|C) = sum_c T[C][c] (e 0|c):
+      //   gamma[t][C] = sum_c T[C][c] sum_e Dp[e] (e 0|c)_t,   Dp = w M^T D_pair
+      //   y[e]       += sum_{t,c} (e 0|c)_t cp[t][c],           cp = T^T c_t
+      // and J += wj M y per sub-pair once all its tiles are done
+      // (jeng_finish_kernel).  No ket transform, HRR or bra transform per triple.
+      const int nk = d.nkrow, ncc = d.ncc, nC = d.nC;
+      double* Dp = sm + d.dscr;       // [nk]
+      double* Cp = Dp + nk;           // [tv][ncc]
+      double* gq = Cp + T * ncc;      // [tv][ncc]
+      if (d.gacc)
+        for (int e = tid; e < nk; e += kThreads) Dp[e] = __ldg(d.jD + sub * nk + e);
+      if (d.Jacc)
+        for (int i = tid; i < tv * ncc; i += kThreads) {
+          const int t = i / ncc, c = i - t * ncc;
+          const double* cv = d.cvec + __ldg(d.aux_ao + aux0 + t);
+          double v = 0.0;
+          for (int q = __ldg(d.ktptr + c); q < __ldg(d.ktptr + c + 1); ++q) {
+            const int2 e = __ldg(d.ktent + q);
+            v = fma(__ldg(d.pal + e.y), __ldg(cv + e.x), v);
+          }
+          Cp[i] = v;
+        }
+      __syncthreads();
+      const Buf gb = d.Gb;
+      FDiv fc;
+      fc.init(ncc);
+      if (d.gacc) {
+        seg_dot(tv * ncc, nk,
+                [&](int o, int r, double acc) {
+                  const int t = (int)fc.div(o), c = o - t * ncc;
+                  return fma(sm[BUF_T(gb, r * ncc + c, t)], Dp[r], acc);
+                },
+                [&](int o, double v) { gq[o] = v; }, true);
+        __syncthreads();
+        FDiv fCC;
+        fCC.init(nC);
+        for (int i = tid; i < tv * nC; i += kThreads) {
+          const int t = (int)fCC.div(i), C = i - t * nC;
+          double v = 0.0;
+          for (int q = __ldg(d.kptr + C); q < __ldg(d.kptr + C + 1); ++q) {
+            const int2 e = __ldg(d.kent + q);
+            v = fma(__ldg(d.pal + e.y), gq[t * ncc + e.x], v);
+          }
+          fix_add(d.gacc + 2 * (__ldg(d.aux_ao + aux0 + t) + C), v);
+        }
+      }
+      if (d.Jacc)
+        seg_dot(nk, tv * ncc,
+                [&](int o, int r, double acc) {
+                  const int t = (int)fc.div(r), c = r - t * ncc;
+                  return fma(sm[BUF_T(gb, o * ncc + c, t)], Cp[r], acc);
+                },
+                [&](int o, double v) { fix_add(d.jY + 2 * (sub * nk + o), v); });
+      return;
+    }
     // ---- ket: Cartesian -> solid harmonic.  With targets across lanes
     // (mode 1) the items run C-major, so a warp's lanes share one C and with
     // it the loop trip count (a warp instruction costs the same whatever the
@@ -589,108 +760,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       }
     }
     __syncthreads();
-    // ---- HRR (Eq. hrr) round by round: each row is dst = sum_t coef_t src_t
-    // over 2 terms (one quantum moved, Eq. hrr) or 3-4 terms (two quanta,
-    // Sec. 2.5.5), the coefficients products of AB components
-    for (int j = 1; j <= d.nhrr; ++j) {
-      FDiv fX, fC;
-      const int nx = d.hrows[j] * d.nC;
-      fX.init(nx);
-      fC.init(d.nC);
-      const unsigned n = (unsigned)(T * nx);
-      const Buf hi = d.H[j - 1], ho = d.H[j];
-      const double* abp = sm + d.ab_base;
-      for (unsigned w = tid; w < n; w += kThreads) {
-        int t, x;
-        dec2(w, mode, fT, fX, t, x);
-        if (t >= tv) continue;
-        const int r = (int)fC.div(x), C = x - r * d.nC;
-        const uint4 e = __ldg(d.htab + d.hstart[j] + r);
-        const unsigned nt = e.x >> 16;
-        double v = fma(abp[(e.w >> 4) & 0xF], sm[BUF_T(hi, (int)(e.y >> 16) * d.nC + C, t)],
-                       sm[BUF_T(hi, (int)(e.y & 0xFFFF) * d.nC + C, t)]);
-        if (nt > 2) v = fma(abp[(e.w >> 8) & 0xF], sm[BUF_T(hi, (int)(e.z & 0xFFFF) * d.nC + C, t)], v);
-        if (nt > 3) v = fma(abp[(e.w >> 12) & 0xF], sm[BUF_T(hi, (int)(e.z >> 16) * d.nC + C, t)], v);
-        sm[BUF_T(ho, (int)(e.x & 0xFFFF) * d.nC + C, t)] = v;
-      }
-      __syncthreads();
-    }
-    // ---- optional solid-harmonic bra
-    Buf cur = d.H[d.nhrr];
-    if (d.nbA) {
-      FDiv fX, fC, fB;
-      const int nx = d.nbA * d.nC;
-      fX.init(nx);
-      fC.init(d.nC);
-      fB.init(d.ncB);
-      const unsigned n = (unsigned)(T * nx);
-      for (unsigned w = tid; w < n; w += kThreads) {
-        int t, x;
-        dec2(w, mode, fT, fX, t, x);
-        if (t >= tv) continue;
-        const int row = (int)fC.div(x), C = x - row * d.nC;
-        const int A = (int)fB.div(row), ib = row - A * d.ncB;
-        const int q0 = __ldg(d.baptr + A), q1 = __ldg(d.baptr + A + 1);
-        double s;
-        const int2 e0 = __ldg(d.baent + q0);
-        if (q1 - q0 == 1 && e0.y == 0) {
-          s = sm[BUF_T(cur, (e0.x * d.ncB + ib) * d.nC + C, t)];
-        } else {
-          s = 0.0;
-          for (int q = q0; q < q1; ++q) {
-            const int2 e = __ldg(d.baent + q);
-            s = fma(__ldg(d.pal + e.y), sm[BUF_T(cur, (e.x * d.ncB + ib) * d.nC + C, t)], s);
-          }
-        }
-        sm[BUF_T(d.BA, x, t)] = s;
-      }
-      __syncthreads();
-      cur = d.BA;
-    }
-    if (d.nbB) {
-      // items B-slowest in mode 1: a warp's lanes share B's trip count
-      FDiv fX, fC, fB, fAC;
-      const int nx = d.nbB * d.nC;
-      const int nBs = d.nB, nAC = (d.nbB / d.nB) * d.nC;
-      fX.init(nx);
-      fC.init(d.nC);
-      fB.init(nBs);
-      fAC.init(nAC);
-      const unsigned n = (unsigned)(T * nx);
-      for (unsigned w = tid; w < n; w += kThreads) {
-        int t, x;
-        dec2(w, mode, fT, fX, t, x);
-        if (t >= tv) continue;
-        int A, B, C;
-        if (mode == 0) {
-          const int row = (int)fC.div(x);
-          C = x - row * d.nC;
-          A = (int)fB.div(row);
-          B = row - A * nBs;
-        } else {
-          B = (int)fAC.div(x);
-          const int rem = x - B * nAC;
-          A = (int)fC.div(rem);
-          C = rem - A * d.nC;
-        }
-        x = (A * nBs + B) * d.nC + C;
-        const int q0 = __ldg(d.bbptr + B), q1 = __ldg(d.bbptr + B + 1);
-        double s;
-        const int2 e0 = __ldg(d.bbent + q0);
-        if (q1 - q0 == 1 && e0.y == 0) {
-          s = sm[BUF_T(cur, (A * d.ncB + e0.x) * d.nC + C, t)];
-        } else {
-          s = 0.0;
-          for (int q = q0; q < q1; ++q) {
-            const int2 e = __ldg(d.bbent + q);
-            s = fma(__ldg(d.pal + e.y), sm[BUF_T(cur, (A * d.ncB + e.x) * d.nC + C, t)], s);
-          }
-        }
-        sm[BUF_T(d.BB, x, t)] = s;
-      }
-      __syncthreads();
-      cur = d.BB;
-    }
+    Buf cur = hrr_and_bra(d, sm, T, tv, mode, fT);
     if (d.digest == 3) {
       // ---- matrix store (2-centre metric (P|Q) = (P 1|Q), nB = 1): element
       // (t, A, C) of the tile goes to out[(ao_pair + A) * ldD + ao_ket + C]
@@ -766,7 +836,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       }
       return;
     }
-    if (kMulti) {
+    if (kMulti && d.digest == 4) {
       // ---- DF-J digestion for nd <= 8 densities at once, as two small GEMMs
       // on FP64 tensor-core tiles (m8n8k4), with M rows per warp tile:
       //   gamma[d][t][C] = wg * sum_s I[t][s][C] Ds[s][d]    (M = tv*nC, K = nAB)
@@ -914,10 +984,86 @@ __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__
   for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body<false>(d, tile, sm);
 }
 
-// The same for DF-J launches digesting several densities (digest == 4).
+// The same for DF-J launches digesting several densities (digest == 4) or
+// contracting at the (e 0|c) level (digest == 5).
 __global__ void __launch_bounds__(kThreads) eri3c_multi_kernel(const __grid_constant__ ClassDesc d) {
   extern __shared__ double sm[];
   for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body<true>(d, tile, sm);
+}
+
+// The bra map M of every sub-pair of a launch (digest 5): HRR and bra
+// transforms applied to the unit vectors, i.e. the class stages with the nkrow
+// rows of the identity in place of (e 0|C) (the descriptor has nC = nkrow,
+// one "triple" per tile).  M[sub][s][e], s the block's storage index.
+__global__ void __launch_bounds__(kThreads) jeng_matrix_kernel(const __grid_constant__ ClassDesc d) {
+  extern __shared__ double sm[];
+  const unsigned tid = threadIdx.x;
+  const int nk = d.nkrow, nAB = d.onA * d.onB;
+  FDiv fT;
+  fT.init(1);
+  for (long long sub = blockIdx.x; sub < d.nsub; sub += gridDim.x) {
+    const long long pair = __ldg(d.subpairs + sub).x;
+    __syncthreads();
+    if (tid < 13) {
+      const double sg = d.orient ? -1.0 : 1.0;
+      const double x = sg * d.pairab[pair * 3], y = sg * d.pairab[pair * 3 + 1], z = sg * d.pairab[pair * 3 + 2];
+      const int ax = tid >= 1 && tid <= 9 ? (int)(tid - 1) % 3 : 0;
+      const double u = ax == 0 ? x : (ax == 1 ? y : z);
+      double v = 1.0;
+      if (tid >= 1 && tid <= 3) v = u;
+      else if (tid >= 4 && tid <= 6) v = 2.0 * u;
+      else if (tid >= 7 && tid <= 9) v = u * u;
+      else if (tid == 10) v = x * y;
+      else if (tid == 11) v = x * z;
+      else if (tid == 12) v = y * z;
+      sm[d.ab_base + tid] = v;
+    }
+    for (int w = tid; w < nk * nk; w += kThreads) sm[BUF_T(d.H[0], w, 0)] = (w / nk == w % nk) ? 1.0 : 0.0;
+    __syncthreads();
+    const Buf cur = hrr_and_bra(d, sm, 1, 1, 1, fT);
+    double* M = d.jM + sub * (long long)nAB * nk;
+    for (int w = tid; w < nAB * nk; w += kThreads) M[w] = sm[BUF_T(cur, w, 0)];
+  }
+}
+
+// Dp[sub][e] = w sum_s D_s M[sub][s][e] (the pair's D block through M^T),
+// one warp per sub-pair.
+__global__ void jeng_dprime_kernel(const __grid_constant__ ClassDesc d) {
+  const int lane = threadIdx.x & 31;
+  const long long sub = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (sub >= d.nsub) return;
+  const int nk = d.nkrow, nA = d.onA, nB = d.onB, nAB = nA * nB;
+  const long long pair = __ldg(d.subpairs + sub).x;
+  const int4 pao = __ldg(d.pair_ao + pair);
+  const double w = pao.z ? 1.0 : 2.0;
+  const double* M = d.jM + sub * (long long)nAB * nk;
+  for (int e = lane; e < nk; e += 32) {
+    double v = 0.0;
+    for (int s = 0; s < nAB; ++s) {
+      const int A = d.orient ? s % nA : s / nB, B = d.orient ? s / nA : s % nB;
+      v = fma(__ldg(d.D + (long long)(pao.x + A) * d.ldD + pao.y + B), M[s * nk + e], v);
+    }
+    d.jD[sub * nk + e] = w * v;
+  }
+}
+
+// J_pair += wj M y for every sub-pair (y from the fixed-point accumulators),
+// one warp per sub-pair.
+__global__ void jeng_finish_kernel(const __grid_constant__ ClassDesc d) {
+  const int lane = threadIdx.x & 31;
+  const long long sub = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (sub >= d.nsub) return;
+  const int nk = d.nkrow, nA = d.onA, nB = d.onB, nAB = nA * nB;
+  const long long pair = __ldg(d.subpairs + sub).x;
+  const int4 pao = __ldg(d.pair_ao + pair);
+  const double wj = pao.z ? 0.5 : 1.0;
+  const double* M = d.jM + sub * (long long)nAB * nk;
+  for (int s = lane; s < nAB; s += 32) {
+    double v = 0.0;
+    for (int e = 0; e < nk; ++e) v = fma(M[s * nk + e], fix_decode(d.jY + 2 * (sub * nk + e)), v);
+    const int A = d.orient ? s % nA : s / nB, B = d.orient ? s / nA : s % nB;
+    fix_add(d.Jacc + 2 * ((long long)(pao.x + A) * d.ldD + pao.y + B), wj * v);
+  }
 }
 
 // Persistent form for mixed workloads: every CTA pulls (descriptor, tile)
@@ -996,10 +1142,31 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (d.digest == 4)
+  if (d.digest >= 4)
     eri3c_multi_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);
   else
     eri3c_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jeng_matrix(const ClassDesc& d, int grid, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(jeng_matrix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  jeng_matrix_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jeng_pair(const ClassDesc& d, int finish, cudaStream_t st) {
+  if (d.nsub == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((d.nsub + 7) / 8);
+  if (finish)
+    jeng_finish_kernel<<<grid, 256, 0, st>>>(d);
+  else
+    jeng_dprime_kernel<<<grid, 256, 0, st>>>(d);
   return cudaGetLastError();
 }
 

@@ -83,6 +83,8 @@ struct ClassDesc {
   const double* pal;       // coefficient palette
   const int* kptr;         // ket CSR by C
   const int2* kent;        // (c, coef_id)
+  const int* ktptr;        // the same transform transposed: CSR by c
+  const int2* ktent;       // (C, coef_id)
   // HRR rows {dst | nterm << 16, src0 | src1 << 16, src2 | src3 << 16, 4-bit
   // codes of the terms' AB-product coefficients}: dst = sum_t coef_t src_t
   const uint4* htab;
@@ -130,6 +132,12 @@ struct ClassDesc {
   unsigned long long* gacc;
   unsigned long long* Jacc;
   unsigned long long* facc;
+  // contraction at the (e 0|c) level (digest == 5, the DF-J analogue of a
+  // J-engine): per sub-pair of the launch the bra map M [nAB][nkrow] (HRR and
+  // bra transforms), Dp = w M^T D [nkrow] and the fixed-point y [nkrow]
+  double* jM;
+  double* jD;
+  unsigned long long* jY;
   long long ldD;           // row stride of D and J
   const double* D;
   const double* cvec;
@@ -179,6 +187,8 @@ struct ClassTables {
   std::vector<double> pal;
   std::vector<int> kptr;
   std::vector<int2> kent;
+  std::vector<int> ktptr;       // ket transform transposed (CSR by Cartesian c)
+  std::vector<int2> ktent;
   int nkrow;
   int nhrr = 0, hrr2 = 0;      // HRR rounds; 1 if rounds move two quanta (Sec. 2.5.5)
   std::vector<int4> erow_xyz;  // Cartesian exponents of the nkrow round-0 rows
@@ -209,6 +219,8 @@ struct DevClass {
   const double* pal;
   const int* kptr;
   const int2* kent;
+  const int* ktptr;
+  const int2* ktent;
   const uint4* htab;
   const int* baptr;
   const int2* baent;
@@ -236,8 +248,8 @@ void fill_desc_common(ClassDesc& d, const ClassTables& ct, const DevClass& dc, c
                       const double* boys_mid, int orient, int kmax, int Kab_rec, int Kc, const LaunchShape& sh);
 // Device pointers of every class table inside one uploaded blob laid out by
 // class_blob (same offsets on host and device).
-std::vector<char> class_blob(const ClassTables& ct, size_t offs[16]);
-void class_blob_pointers(DevClass& dc, const void* dev_blob, const size_t offs[16]);
+std::vector<char> class_blob(const ClassTables& ct, size_t offs[18]);
+void class_blob_pointers(DevClass& dc, const void* dev_blob, const size_t offs[18]);
 
 // planner entry points (plan.cu)
 const ClassTables& class_tables(int la, int lb, int lc, int bra_pure);  // HRR variant from the hints

@@ -115,7 +115,7 @@ __global__ void noalloc_orient(const int32_t* __restrict__ pairs, long long npai
 struct NaBlob {
   std::vector<char> bytes;
   size_t base[2] = {0, 0};
-  size_t offs[2][16] = {};
+  size_t offs[2][18] = {};
 };
 
 const NaBlob& na_blob(int la, int lb, int lc, int bra_pure, int split) {

@@ -421,6 +421,14 @@ ClassTables build(int la, int lb, int lc, int bra_pure, int hrr2) {
     }
     ct.kptr[C + 1] = (int)ct.kent.size();
   }
+  ct.ktptr.assign(ct.ncc + 1, 0);
+  for (int c = 0; c < ct.ncc; ++c) {
+    for (int C = 0; C < ct.nC; ++C) {
+      double v = Tc[C * ct.ncc + c];
+      if (v != 0.0) ct.ktent.push_back(int2{C, (int)pal_id(ct.pal, palids, v)});
+    }
+    ct.ktptr[c + 1] = (int)ct.ktent.size();
+  }
 
   // ---------------- bra transforms ----------------
   ct.nbA = ct.nbB = 0;

@@ -109,3 +109,32 @@ def test_dfj_and_gradient_are_bitwise_reproducible(lx):
         for a, b in zip(r, runs[0]):
             assert np.array_equal(a, b)
     assert np.array_equal(runs[0][1], runs[0][1].T)
+
+
+@pytest.mark.parametrize("shape,recipe_aux", [((2, 2, 1), "dfj"), ((2, 1, 1), "grad")])
+def test_dfj_contracted_at_intermediates(lx, shape, recipe_aux):
+    """The (e 0|c)-level contraction (LX3C_DFJ_CONTRACT: the pair's bra map
+    formed once, D and c contracted before the ket transform, HRR and bra
+    transforms) gives the per-integral digestion's gamma and J to rounding,
+    and the binary128 oracle's."""
+    aux = W.AUX_RECIPE_DFJ if recipe_aux == "dfj" else W.AUX_RECIPE_GRAD
+    orb = W.ORB_RECIPE_DFJ if recipe_aux == "dfj" else W.ORB_RECIPE_SMALL
+    cl = W.cluster(shape, orb, aux, seed=75)
+    D, c = inputs(cl, 12)
+    Dt, ct = torch.tensor(D, device="cuda"), torch.tensor(c, device="cuda")
+    plain = lx.DFJPlan(cl.orb, cl.aux, 1e-12)
+    jeng = lx.DFJPlan(cl.orb, cl.aux, 1e-12, contract=True)
+    assert jeng.ntasks == plain.ntasks and jeng.flops < plain.flops
+    g0, J0 = plain.execute(Dt, ct)
+    g1, J1 = jeng.execute(Dt, ct)
+    g0, J0, g1, J1 = (x.cpu().numpy() for x in (g0, J0, g1, J1))
+    assert normwise(g1, g0) < 1e-12
+    assert normwise(J1, J0) < 1e-12
+    np.testing.assert_allclose(J1, J1.T, rtol=0, atol=1e-14 * np.abs(J1).max())
+    go, Jo = oracle.dfj(cl.orb, cl.aux, D, c, tasks=jeng.tasks(), mode="quad")
+    assert normwise(g1, go) < 1e-12
+    assert normwise(J1, Jo) < 1e-12
+    # gamma alone, J alone, and the energy path
+    g2, _ = jeng.execute(Dt, ct, outputs="gamma")
+    _, J2 = jeng.execute(Dt, ct, outputs="J")
+    assert np.array_equal(g2.cpu().numpy(), g1) and np.array_equal(J2.cpu().numpy(), J1)
