@@ -494,7 +494,17 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
         fill_desc_common(dm, ctm, *dc, dev_boys_tab(ds), dev_boys_mid(ds), o, kmax[o], Kab, g.Kc, shm);
         ClassDesc dj = d;
         dj.digest = 5;
-        dj.dscr = place_epilogue_scratch(dj, ct->nkrow + 2LL * dj.T * ct->ncc);
+        {
+          // the gather output (X region) is live in this epilogue; the P
+          // accumulators before it (Y region) are dead after the gather
+          const long long need = ct->nkrow + 2LL * dj.T * ct->ncc;
+          if (need <= (long long)dj.V.base - dj.P.base) {
+            dj.dscr = dj.P.base;
+          } else {
+            dj.dscr = dj.smem_doubles;
+            dj.smem_doubles += (int)need;
+          }
+        }
         if ((long long)dm.smem_doubles * 8 <= 232448 && (long long)dj.smem_doubles * 8 <= 232448) {
           dm.npair = np; dm.naux = na; dm.nsub = d.nsub; dm.subpairs = d.subpairs; dm.pairab = g.d_pairab;
           L.jeng = true;
