@@ -248,7 +248,7 @@ def run_ours(args, rank, world, dist):
                roofline=dict(bound="alu", achieved=round(ach, 2), peak=round(FP64_PEAK_GFLOPS, 1), unit="GFLOP/s",
                              frac=round(ach / FP64_PEAK_GFLOPS, 4), traffic=traffic,
                              kernel="eri3c_kernel, class (%d%d|%d) K_ab=%d" % plans[dom]["cls"],
-                             peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)",
+                             peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                              flops_per_launch=plans[dom]["flops"], launch_ms=round(dms, 3)),
                l3_frac=dict(classes=len(l3), min=min(l3) if l3 else None,
                             median=statistics.median(l3) if l3 else None,
@@ -309,13 +309,15 @@ def event_ms(fn, reps=1):
 
 
 def with_clocks(dev, fn):
+    """fn()'s dict with a compact clock record of its run: [median SM MHz,
+    samples, throttle reasons]."""
     clocks = ClockSampler(dev.index)
     clocks.start()
     try:
         res = fn()
     finally:
         clk = clocks.stop()
-    res["clocks"] = clk
+    res["clocks"] = [clk.get("sm_mhz"), clk.get("samples", 0), clk.get("reasons", [])]
     return res
 
 
@@ -333,7 +335,7 @@ def extra_config1(dev):
     reps = 500
     ms = statistics.median(t / reps for t in event_ms(lambda: [plan.execute(out) for _ in range(reps)], 40))
     fl = lx.class_flops(1, 1, 2, 1, 1, True) * plan.npair * plan.naux
-    return dict(workload="(pp|d) K=1, 64 pairs x 32 kets", integrals=int(plan.total),
+    return dict(workload="(pp|d) 64x32", integrals=int(plan.total),
                 ms=round(ms, 4), gints_s=round(plan.total / ms / 1e6, 4),
                 frac=round(fl / ms / 1e6 / FP64_PEAK_GFLOPS, 4), launches=plan.launches, reps=40 * reps)
 
@@ -356,7 +358,7 @@ def extra_dfj(dev):
     fused = event_ms(lambda: plan.execute(D, c, gamma, J))[0]
     gonly = event_ms(lambda: plan.execute(D, c, gamma, None, outputs="gamma"))[0]
     jonly = event_ms(lambda: plan.execute(D, c, None, J, outputs="J"))[0]
-    return dict(workload="DF-J, 256 atoms, 4s3p2d1f / 10s7p5d3f2g1h, screen 1e-12", nao=plan.nao, naux_ao=plan.naux_ao,
+    return dict(workload="DF-J 256 atoms", nao=plan.nao, naux_ao=plan.naux_ao,
                 screened_triples=plan.ntasks, integrals=plan.nint, tile_fill=round(plan.tile_fill, 4),
                 setup_s=round(setup, 2), first_build_s=round(first / 1e3, 3), fused_s=round(fused / 1e3, 3),
                 gamma_only_s=round(gonly / 1e3, 3), J_only_s=round(jonly / 1e3, 3),
@@ -385,7 +387,7 @@ def extra_batch(dev):
     m0 = event_ms(lambda: b.execute(0))[0]
     m1 = event_ms(lambda: b.execute(1))[0]
     fl = info["flops"]
-    return dict(workload="16 molecules, 20-400 atoms, 3s2p2d1f1g (25% of shells) / 8s6p5d4f3g2h1i, DF-J",
+    return dict(workload="16 molecules, 20-400 atoms",
                 screened_triples=info["tasks"], plan_s=round(plan_s, 2), bind_capture_s=round(bind_s, 2),
                 graph_branches_s=round(m2 / 1e3, 3), per_class_s=round(m0 / 1e3, 3),
                 graph_persistent_s=round(m1 / 1e3, 3),
@@ -417,7 +419,7 @@ def extra_grad(dev):
     bwd = statistics.median(event_ms(lambda: plan.gradient(D, c, grad), 2))
     both = statistics.median(event_ms(lambda: (plan.energy(D, c), plan.gradient(D, c, grad)), 2))
     plain = statistics.median(event_ms(lambda: plan.execute(D, c, gamma, J), 2))
-    return dict(workload="64 atoms, 3s2p2d1f1g / 8s6p5d4f3g2h, E = c^T gamma, dE/dR",
+    return dict(workload="dE/dR, 64 atoms",
                 screened_triples=plan.ntasks, fwd_ms=round(fwd, 2), bwd_ms=round(bwd, 2), fwd_bwd_ms=round(both, 2),
                 plain_fwd_gamma_J_ms=round(plain, 2), fwd_bwd_over_fwd=round(both / fwd, 3),
                 bwd_frac=round(plan.grad_flops / bwd / 1e6 / FP64_PEAK_GFLOPS, 4),
@@ -441,9 +443,9 @@ def extra_dfj_multi(dev):
     plan.execute_multi(D8, c8)
     t1 = statistics.median(event_ms(lambda: plan.execute(D8[0], c8[0], gamma, J), 3))
     t8 = statistics.median(event_ms(lambda: plan.execute_multi(D8, c8), 3))
-    return dict(workload="DF-J, 32 atoms of the 256-atom recipe, gamma+J", screened_triples=plan.ntasks,
+    return dict(workload="DF-J 32 atoms", screened_triples=plan.ntasks,
                 nd1_ms=round(t1, 2), nd8_ms=round(t8, 2), per_density_ms_nd8=round(t8 / 8, 2),
-                per_density_speedup=round(t1 / (t8 / 8), 3), digest="nd=8: mma.sync m8n8k4 f64 tiles")
+                per_density_speedup=round(t1 / (t8 / 8), 3))
 
 
 def extra_metric(dev):
@@ -465,7 +467,7 @@ def extra_metric(dev):
     b = torch.tensor(np.random.default_rng(6).standard_normal(n), device=dev)
     ts = statistics.median(event_ms(lambda: lx.cholesky_solve(V, b), 3))
     chol_flops = n ** 3 / 3.0
-    return dict(workload="metric of the 256-atom aux basis (10s7p5d3f2g1h per atom)", naux_ao=n,
+    return dict(workload="metric, 256-atom aux basis", naux_ao=n,
                 metric_ms=round(tv, 2), metric_frac=round(mp.flops / tv / 1e6 / FP64_PEAK_GFLOPS, 4),
                 cholesky_ms=round(tc, 2), cholesky_gflops=round(chol_flops / tc / 1e6, 1),
                 cholesky_frac=round(chol_flops / tc / 1e6 / FP64_PEAK_GFLOPS, 4), cholesky_info=int(info[0]),
@@ -486,7 +488,7 @@ def run_extras(args, dev):
         runs = [lx.fp64_rate(1 << 15) for _ in range(3)]
         g, ms = max(runs)
         return dict(gflops=round(g, 1), ms=round(ms, 2), frac_of_derived=round(g / FP64_PEAK_GFLOPS, 4),
-                    method="lx3c_fp64_rate, best of 3")
+                    method="lx3c_fp64_rate")
     out["fp64_peak_measured"] = with_clocks(dev, peak)
     for n in names:
         if n not in EXTRAS:
@@ -555,6 +557,35 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def make_line(args, res, classes, world, cpu, extras):
+    """The bench's one JSON line (kept under 4 KB: the per-class table goes to
+    --per-class-out, the line keeps the slowest and the lowest-fraction classes)."""
+    value = res["total_int"] / (res["ms"] / 1e3) / 1e9
+    top = sorted(res["table"], key=lambda r: -r["ms"])[:6]
+    low = sorted((r for r in res["table"] if sum(r["cls"][:3]) >= 3), key=lambda r: r["frac"])[:4]
+    line = dict(
+        metric="3c-ERI Gints/s FP64 per (La,Lb,Lc,K)", value=round(value, 4), unit="Gints/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=round(res["ms"] / args.steps, 2),
+        higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+        data="synthetic (per-class sweep recipe, seeded; no public dataset)",
+        config=dict(sweep_config(args, classes, world),
+                    tile_shapes=("planner default + %d tuned hints (shape_hints_gb300.txt)" % getattr(args, "hints", 0)
+                                 if getattr(args, "hints", 0) else "planner default"),
+                    hrr=("1-q rounds + %d tuned 2-q classes (hrr_hints_gb300.txt)" % getattr(args, "hrr_hints", 0)
+                         if getattr(args, "hrr_hints", 0) else "1-q rounds")),
+        roofline=res["roofline"], cpu_baseline=cpu, clocks=res["clocks"], gpu_launches=res["launches"],
+        fp64_tflops_sweep=round(res["total_flops"] / (res["ms"] / 1e3) / 1e12, 4),
+        l3_roofline_frac=res["l3_frac"],
+        slowest_classes=[[*r["cls"], r["ms"], r["frac"]] for r in top],
+        lowest_frac_l3_classes=[[*r["cls"], r["ms"], r["frac"]] for r in low],
+        class_row="[la,lb,lc,K_ab,ms,frac]",
+    )
+    if "e2e" in res:
+        line["e2e"] = res["e2e"]
+    line.update(extras)
+    return line
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -576,31 +607,9 @@ def main():
     if not args.no_cpu:
         c = oracle_sample(classes, args, args.cpu_seconds)
         cpu = {k: c[k] for k in ("value", "unit", "cores", "kind", "sample")}
-    value = res["total_int"] / (res["ms"] / 1e3) / 1e9
-    top = sorted(res["table"], key=lambda r: -r["ms"])[:8]
-    low = sorted((r for r in res["table"] if sum(r["cls"][:3]) >= 3), key=lambda r: r["frac"])[:5]
     import torch
     extras = run_extras(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
-    line = dict(
-        metric="3c-ERI Gints/s FP64 per (La,Lb,Lc,K)", value=round(value, 4), unit="Gints/s", n_gpus=world,
-        steps=args.steps, warmup=args.warmup, ms_per_step=round(res["ms"] / args.steps, 2),
-        higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-        data="synthetic (per-class sweep recipe, seeded; no public dataset)",
-        config=dict(sweep_config(args, classes, world),
-                    tile_shapes=("planner default + %d tuned hints (shape_hints_gb300.txt)" % getattr(args, "hints", 0)
-                                 if getattr(args, "hints", 0) else "planner default"),
-                    hrr=("1-q rounds + %d tuned 2-q classes (hrr_hints_gb300.txt)" % getattr(args, "hrr_hints", 0)
-                         if getattr(args, "hrr_hints", 0) else "1-q rounds")),
-        roofline=res["roofline"], cpu_baseline=cpu, clocks=res["clocks"], gpu_launches=res["launches"],
-        fp64_tflops_sweep=round(res["total_flops"] / (res["ms"] / 1e3) / 1e12, 4),
-        l3_roofline_frac=res["l3_frac"],
-        slowest_classes=[[*r["cls"], r["ms"], r["frac"]] for r in top],
-        lowest_frac_l3_classes=[[*r["cls"], r["ms"], r["frac"]] for r in low],
-        class_row="[la, lb, lc, K_ab, ms, FP64 fraction]",
-    )
-    if "e2e" in res:
-        line["e2e"] = res["e2e"]
-    line.update(extras)
+    line = make_line(args, res, classes, world, cpu, extras)
     if args.per_class_out:
         with open(args.per_class_out, "w") as f:
             json.dump(res["table"], f)
