@@ -481,11 +481,21 @@ void lx3c_batch_destroy(lx3c_batch* batch);
  * 27 MB that every GPU loading the library holds until process exit.
  * Limits: npair <= 65536, npair*ka*kb <= 65536, naux*kc <= 65536; larger
  * problems are rejected with LX3C_ENOTSUP and nothing is launched.
- * The first call on a device copies the Boys table into that array
- * (synchronously); make that first call before any stream capture.  All calls
- * share the array and each overwrites it: calls that overlap on the GPU (for
- * instance on different streams) race; calls on one stream are ordered.
- * Asynchronous on `stream` otherwise; no device memory is allocated or freed.
+ * First call on a device (once per process and device): it looks up the
+ * array's device address, builds the Boys table on the host and copies it and
+ * the constant tables in with synchronous copies (cudaMemcpy,
+ * cudaMemcpyToSymbol), which wait for the device.  Make that first call before
+ * any stream capture begins.
+ * Every call: the class's index tables (both orientations, at most 4 MB, held
+ * in host memory the library keeps for the process) are copied into the array
+ * by cudaMemcpyAsync from pageable host memory.  CUDA stages such a copy
+ * through a buffer of its own, so the call can return only after the copy is
+ * staged and may first wait for work already queued on `stream`; the
+ * precompute and integral kernels are then queued on `stream` and the call
+ * returns without waiting for them.
+ * All calls share the array and each overwrites it: calls that overlap on the
+ * GPU (for instance on different streams) race; calls on one stream are
+ * ordered.  No device memory is allocated or freed, on any call.
  */
 lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb, int kc, int bra_pure,
                                const int64_t* orb_off, const double* orb_xyz, const double* orb_exps,

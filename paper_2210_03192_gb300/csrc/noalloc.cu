@@ -194,7 +194,8 @@ extern "C" lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb
   int* prim = (int*)(base + kOffPrim);
   // class tables of both orientations, packed into the table region from a
   // host copy kept for the life of the process (the copy's source outlives
-  // the call)
+  // the call).  The source is pageable memory: CUDA stages the copy, so this
+  // call may wait for work already queued on st before it returns.
   const ClassTables* cts[2];
   const NaBlob* nb = nullptr;
   try {

@@ -47,8 +47,7 @@ def test_gpu_arm_line_stays_small():
     res = dict(ms=1234567.8, total_int=192675840000 * 20, total_flops=1e15, table=table, clocks=clk,
                launches=38220, roofline=dict(bound="alu", achieved=921.46, peak=1258.6, unit="GFLOP/s", frac=0.7322,
                                              traffic=17140105216, kernel="eri3c_kernel, class (44|6) K_ab=6",
-                                             peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal "
-                                                         "1.25 TFLOP/s FP64)",
+                                             peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                                              flops_per_launch=1707283054592.0, launch_ms=1852.808),
                l3_frac=dict(classes=495, min=0.3585, median=0.5872, at_least_half=411),
                e2e=dict(value=2.2189, unit="Gints/s", h2d_bytes_per_step=398458880,
@@ -63,14 +62,17 @@ def test_gpu_arm_line_stays_small():
                      frac=0.0176, launches=4, reps=20000, clocks=xclk),
         dfj=dict(workload="DF-J 256 atoms", nao=7680, naux_ao=27136,
                  screened_triples=14074753270, integrals=324312871258.0, tile_fill=0.9728, setup_s=8.81,
-                 first_build_s=54.313, fused_s=54.314, gamma_only_s=53.001, J_only_s=53.24, fused_frac=0.4987,
-                 per_integral_fused_s=54.2, per_integral_frac=0.4987, launches=217, clocks=xclk),
+                 fused_s=54.314, gamma_only_s=53.001, J_only_s=53.24, fused_frac=0.4987,
+                 launches=217,
+                 contracted=dict(setup_s=9.12, fused_s=41.234, gamma_only_s=40.123, J_only_s=40.456,
+                                 flops_ratio=0.7123, fused_frac=0.4567, speedup=1.317, launches=870),
+                 clocks=xclk),
         batch=dict(workload="16 molecules, 20-400 atoms",
                    screened_triples=5238364893.0, plan_s=4.99, bind_capture_s=0.61, graph_branches_s=32.432,
                    per_class_s=32.661, graph_persistent_s=58.32,
                    frac=dict(graph_branches=0.4941, per_class=0.4907, graph_persistent=0.2748),
                    launches=dict(per_class=6127, graph_branches_kernel_nodes=6127, graph_persistent_kernel_nodes=3377,
-                                 persistent_tiers=2, graph_launches=1),
+                                 persistent_tiers=2),
                    speedup_graph_vs_per_class=1.007, clocks=xclk),
         grad=dict(workload="dE/dR, 64 atoms", screened_triples=206219480,
                   fwd_ms=1276.6, bwd_ms=5431.13, fwd_bwd_ms=6707.3, plain_fwd_gamma_J_ms=1325.64,
@@ -80,7 +82,8 @@ def test_gpu_arm_line_stays_small():
                     cholesky_frac=0.8666, cholesky_dropped=1234, solve_ms=138.62,
                     launches=dict(metric=48, cholesky=1270, solve=1694), clocks=xclk),
         dfj_multi=dict(workload="DF-J 32 atoms", screened_triples=123456789,
-                       nd1_ms=1234.5, nd8_ms=2345.6, per_density_ms_nd8=293.2, per_density_speedup=4.21, clocks=xclk))
+                       nd1_ms=1234.5, nd8_ms=2345.6, per_density_ms_nd8=293.2, per_density_speedup=4.21,
+                       nd1_contracted_ms=987.65, clocks=xclk))
     line = bench.make_line(A, res, classes, 1, cpu, extras)
     text = json.dumps(line, separators=(",", ":"))
     assert len(text) < 3800, len(text)  # margin below 4 KB
