@@ -169,8 +169,7 @@ def build_plans(classes, args, rank):
     for (la, lb, lc, K) in classes:
         p = rank_problem(la, lb, lc, K, args.npair, args.naux, rank, args.product_k)
         plan = lx.Eri3cPlan(p.orb, p.aux, p.pairs, p.auxs, bra_pure=True)
-        Kab = K * K if not args.product_k else K
-        flops = lx.class_flops(la, lb, lc, Kab, 1, True) * plan.npair * plan.naux
+        flops = plan.flops  # per the orientation each pair runs in
         plans.append(dict(cls=(la, lb, lc, K), plan=plan, prob=p, flops=flops, nint=plan.total))
     return plans
 
@@ -334,7 +333,7 @@ def extra_config1(dev):
     # batches of 500 evaluations, about 1.5 s in all, so the clock sampler sees the load
     reps = 500
     ms = statistics.median(t / reps for t in event_ms(lambda: [plan.execute(out) for _ in range(reps)], 40))
-    fl = lx.class_flops(1, 1, 2, 1, 1, True) * plan.npair * plan.naux
+    fl = plan.flops
     return dict(workload="(pp|d) 64x32", integrals=int(plan.total),
                 ms=round(ms, 4), gints_s=round(plan.total / ms / 1e6, 4),
                 frac=round(fl / ms / 1e6 / FP64_PEAK_GFLOPS, 4), launches=plan.launches, reps=40 * reps)

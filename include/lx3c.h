@@ -117,7 +117,17 @@ lx3c_status lx3c_plan_sizes(const lx3c_plan* plan, int64_t* block, int64_t* tota
  * Launch shape of a plan (for benchmarks and diagnostics).  Writes up to n
  * int64 values: [kernel launches per execute, then for each of the two
  * orientations (recurrences on A, on B): sub-pairs, triples per tile T,
- * primitive chunk G, lane mode, dynamic shared memory bytes, grid size].
+ * primitive chunk G, lane mode, dynamic shared memory bytes, grid size;
+ * then (index 13) the algorithmic flops of one execute, rounded: every
+ * sub-pair's primitive pairs through its orientation's primitive stages and,
+ * per ket shell, its contracted stages (a pair split across the two
+ * orientations pays the contracted stages twice)].
+ *
+ * Orientation: a pair runs in one orientation when one of them keeps the
+ * weighted HRR amplification within the threshold (lx3c_set_orientation_
+ * threshold): the cheaper one (the HRR moving the lower angular momentum)
+ * when it qualifies, else the other; for la == lb the one with the smaller
+ * amplification.  Otherwise its primitive pairs are split by compact centre.
  */
 lx3c_status lx3c_plan_info(const lx3c_plan* plan, int64_t* out, int n);
 
@@ -433,8 +443,9 @@ lx3c_status lx3c_dfj_coulomb(lx3c_dfj* plan, const double* L, int64_t lda, const
  *   alive while the batch is executed), orders the class launches longest
  *   first and captures two CUDA graphs of the whole build (zeroing,
  *   precompute, integrals, J finish): graph 1 runs every (class launch,
- *   tile) work item in persistent kernels, one per shared-memory tier (the
- *   items that fit two CTAs per SM, then the rest), each sized for its
+ *   tile) work item in persistent kernels, one per occupancy tier (the
+ *   items that fit three CTAs per SM of the 40-register persistent kernel,
+ *   then two CTAs of the unrestricted one, then the rest), each sized for its
  *   tier's largest item and pulling items longest first from its own atomic
  *   counter (no CTA waits on another); graph 2 runs the class launches
  *   themselves on four parallel graph branches.  Setup; may

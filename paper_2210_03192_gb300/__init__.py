@@ -88,9 +88,10 @@ class Eri3cPlan:
         nB = (2 * lb + 1) if bra_pure else (lb + 1) * (lb + 2) // 2
         self.shape = (self.npair, self.naux, nA, nB, 2 * lc + 1)
         self.cls = (la, lb, lc)
-        info = np.zeros(13, np.int64)
-        check(L.lx3c_plan_info(self.handle, ptr(info), 13), "lx3c_plan_info")
+        info = np.zeros(14, np.int64)
+        check(L.lx3c_plan_info(self.handle, ptr(info), 14), "lx3c_plan_info")
         self.launches = int(info[0])
+        self.flops = float(info[13])  # algorithmic flops of one execute, per chosen orientation
         self.shapes = [dict(nsub=int(info[1 + 6 * o]), T=int(info[2 + 6 * o]), G=int(info[3 + 6 * o]),
                             mode=int(info[4 + 6 * o]), smem=int(info[5 + 6 * o]), grid=int(info[6 + 6 * o]))
                        for o in range(2)]

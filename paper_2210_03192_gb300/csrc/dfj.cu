@@ -40,10 +40,10 @@ cudaError_t launch_aux_precompute(const DevBasis& aux, const int32_t* auxs, long
 cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st);
 int eri3c_occupancy(int smem_bytes);
 cudaError_t launch_persistent(const ClassDesc* descs, const int2* work, long long nwork, unsigned long long* counter,
-                              int grid, int smem_bytes, cudaStream_t st);
+                              int grid, int smem_bytes, int three, cudaStream_t st);
 cudaError_t launch_jeng_matrix(const ClassDesc& d, int grid, cudaStream_t st);
 cudaError_t launch_jeng_pair(const ClassDesc& d, int finish, cudaStream_t st);
-int persistent_occupancy(int smem_bytes);
+int persistent_occupancy(int smem_bytes, int three);
 }  // namespace lx3c
 
 using namespace lx3c;
@@ -96,7 +96,7 @@ __global__ void symmetrize(double* J, long long n) {
 // out[i] = value of the fixed-point accumulator acc[i] (gamma, gradient)
 __global__ void fix_finish(const unsigned long long* __restrict__ acc, long long n, double* __restrict__ out) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = fix_decode(acc + 2 * i);
+  if (i < n) out[i] = fix_decode(acc + kFixWords * i);
 }
 
 // J[i][j] = A[i][j] + A[j][i] from the accumulated unique-pair blocks A (the
@@ -105,7 +105,7 @@ __global__ void fix_finish(const unsigned long long* __restrict__ acc, long long
 __global__ void fix_finish_J(const unsigned long long* __restrict__ acc, long long n, double* __restrict__ J) {
   const long long i = blockIdx.y * (long long)blockDim.y + threadIdx.y;
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n && j < n) J[i * n + j] = fix_decode(acc + 2 * (i * n + j)) + fix_decode(acc + 2 * (j * n + i));
+  if (i < n && j < n) J[i * n + j] = fix_decode(acc + kFixWords * (i * n + j)) + fix_decode(acc + kFixWords * (j * n + i));
 }
 
 cudaError_t launch_fix_finish(const unsigned long long* acc, long long n, double* out, cudaStream_t st) {
@@ -398,20 +398,25 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
       p->groups.push_back(std::move(g));
     }
   }
+  // contributions per atom to the gradient's fixed-point accumulators
+  std::vector<double> fadds(std::max(p->natom, 1), 0.0);
   // per group: orientation split, tiles, device lists
   for (auto& g : p->groups) {
     const long long np = (long long)g.counts.size(), na = (long long)g.auxs.size();
     const int nbra = (2 * g.la + 1) * (2 * g.lb + 1), nket = 2 * g.lc + 1;
-    double fl = 0;
-    if (lx3c_class_flops(g.la, g.lb, g.lc, g.Ka * g.Kb, g.Kc, 1, &fl)) return LX3C_ENOTSUP;
-    g.flops = (fl + 4.0 * nbra * nket) * (double)g.ntasks;
     g.nint = (double)nbra * nket * (double)g.ntasks;
     std::vector<int4> sub[2];
     std::vector<int> prim[2];
     int kmax[2] = {0, 0}, cmax = 0;
+    int prefer;
+    try {
+      prefer = cheaper_orientation(g.la, g.lb, g.lc, 1, g.Ka * g.Kb, g.Kc);
+    } catch (std::exception& e) {
+      return dfail(LX3C_ENOTSUP, e.what());
+    }
     for (long long i = 0; i < np; ++i) {
       int oa = (int)prim[0].size(), ob = (int)prim[1].size();
-      split_orientation(orb, g.pairs[2 * i], g.pairs[2 * i + 1], g.la, g.lb, prim[0], prim[1]);
+      split_orientation(orb, g.pairs[2 * i], g.pairs[2 * i + 1], g.la, g.lb, prim[0], prim[1], prefer);
       int na_ = (int)prim[0].size() - oa, nb_ = (int)prim[1].size() - ob;
       if (na_) sub[0].push_back(int4{(int)i, oa, na_, 0});
       if (nb_) sub[1].push_back(int4{(int)i, ob, nb_, 0});
@@ -452,6 +457,17 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
       ClassDesc& d = L.desc;
       if (fill_class_desc(d, *ct, *dc, ds, o, kmax[o], Kab, g.Kc, fill_bound(sub[o], g.counts, cmax)) < 0)
         return dfail(LX3C_ENOTSUP, "class does not fit in shared memory");
+      {
+        // executed flops: each sub-pair's primitive pairs through this
+        // orientation's primitive stages, its contracted stages and the
+        // digestion (4 flops per integral) once per kept ket shell
+        double tris = 0, primtris = 0;
+        for (auto& sp : sub[o]) {
+          tris += g.counts[sp.x];
+          primtris += (double)g.counts[sp.x] * sp.z * g.Kc;
+        }
+        g.flops += primtris * ct->flops_prim + tris * (ct->flops_contr + 4.0 * nbra * nket);
+      }
       std::vector<int4> tiles;
       for (size_t s = 0; s < sub[o].size(); ++s) {
         const int cnt = g.counts[sub[o][s].x];
@@ -540,6 +556,9 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
     DCUDA(cudaMalloc(&g.d_aux_atom, na * 4));
     DCUDA(cudaMemcpyAsync(g.d_pair_atoms, pat.data(), np * sizeof(int2), cudaMemcpyHostToDevice, st));
     DCUDA(cudaMemcpyAsync(g.d_aux_atom, aat.data(), na * 4, cudaMemcpyHostToDevice, st));
+    std::vector<double> gket_on_atom(p->natom, 0.0);
+    for (long long q = 0; q < na; ++q)
+      if (aat[q] >= 0) gket_on_atom[aat[q]] += 1.0;
     for (int centre = 0; centre < 2; ++centre)
       for (int plus = 1; plus >= 0; --plus) {
         const int l1 = g.la + (centre == 0 ? (plus ? 1 : -1) : 0), l2 = g.lb + (centre == 1 ? (plus ? 1 : -1) : 0);
@@ -553,9 +572,15 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
         std::vector<int4> dsub[2];
         std::vector<int> dprim[2];
         int dk[2] = {0, 0};
+        int dprefer;
+        try {
+          dprefer = cheaper_orientation(l1, l2, g.lc, 0, Kab, g.Kc);
+        } catch (std::exception& e) {
+          return dfail(LX3C_ENOTSUP, e.what());
+        }
         for (long long i = 0; i < np; ++i) {
           int oa = (int)dprim[0].size(), ob = (int)dprim[1].size();
-          split_orientation(orb, g.pairs[2 * i], g.pairs[2 * i + 1], l1, l2, dprim[0], dprim[1]);
+          split_orientation(orb, g.pairs[2 * i], g.pairs[2 * i + 1], l1, l2, dprim[0], dprim[1], dprefer);
           int na_ = (int)dprim[0].size() - oa, nb_ = (int)dprim[1].size() - ob;
           if (na_) dsub[0].push_back(int4{(int)i, oa, na_, 0});
           if (nb_) dsub[1].push_back(int4{(int)i, ob, nb_, 0});
@@ -577,13 +602,24 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
           ClassDesc& d = L.desc;
           if (fill_class_desc(d, *ct, *dc, ds, o, dk[o], Kab, g.Kc, fill_bound(dsub[o], g.counts, cmax)) < 0)
             return dfail(LX3C_ENOTSUP, "derivative class does not fit in shared memory");
+          {
+            // executed flops of this derivative launch (as for the class
+            // launches) plus its contraction with D, c (2 flops per entry of
+            // the derivative map and ket function)
+            double tris = 0, primtris = 0;
+            for (auto& sp : dsub[o]) {
+              tris += g.counts[sp.x];
+              primtris += (double)g.counts[sp.x] * sp.z * g.Kc;
+            }
+            g.gflops += primtris * ct->flops_prim + tris * (ct->flops_contr + 2.0 * gmap.size() * (2 * g.lc + 1));
+          }
           // entries per partial sum: balances the partial's FMA chain (E (nC+1))
           // against the final sum over the nmax / E partials of an axis
           const int E = std::max(1, std::min(32, (int)std::lround(std::sqrt((double)nmax / (d.nC + 1)))));
           const int nch = std::max(1, (nmax + E - 1) / E);
           const int nAp = 2 * g.la + 1, ncA = ncart(g.la), nBp = 2 * g.lb + 1, ncB = ncart(g.lb);
           d.g_echunk = E;
-          d.g_base = place_epilogue_scratch(d, nAp * ncB + ncA * ncB + (long long)d.T * 3 * nch);
+          d.g_base = place_epilogue_scratch(d, nAp * ncB + ncA * ncB + (long long)d.T * 3 * (nch + 1));
           if (d.smem_doubles * 8 > 232448) return dfail(LX3C_ENOTSUP, "gradient epilogue does not fit");
           d.g_centre = centre;
           d.g_nAp = nAp; d.g_ncA = ncA; d.g_nBp = nBp; d.g_ncB = ncB; d.g_nch = nch;
@@ -591,9 +627,16 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
           d.gmap = dv.d_gmap;
           std::vector<int4> tiles;
           for (size_t s2 = 0; s2 < dsub[o].size(); ++s2) {
-            const int cnt = g.counts[dsub[o][s2].x];
-            for (int a0 = 0; a0 < cnt; a0 += d.T) tiles.push_back(int4{(int)s2, a0, std::min(d.T, cnt - a0), 0});
+            const int pi = dsub[o][s2].x, cnt = g.counts[pi];
+            const int tat = orb->atom[g.pairs[2 * pi + centre]];
+            for (int a0 = 0; a0 < cnt; a0 += d.T) {
+              tiles.push_back(int4{(int)s2, a0, std::min(d.T, cnt - a0), 0});
+              if (tat >= 0) fadds[tat] += 1.0;  // one add per axis per tile
+            }
           }
+          // one add per triple to the ket shell's atom: at most this
+          // launch's sub-pairs times the group's kets on that atom
+          for (int a = 0; a < p->natom; ++a) fadds[a] += (double)dsub[o].size() * gket_on_atom[a];
           L.ntiles = (long long)tiles.size();
           DCUDA(cudaMalloc(&L.d_sub, dsub[o].size() * sizeof(int4)));
           DCUDA(cudaMalloc(&L.d_prim, std::max<size_t>(dprim[o].size(), 1) * sizeof(int)));
@@ -614,12 +657,11 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
           const int occ = eri3c_occupancy(d.smem_doubles * 8);
           L.grid = (int)std::min<long long>(L.ntiles, (long long)dev_nsm(ds) * occ * 8);
         }
-        double fl = 0;
-        lx3c_class_flops(l1, l2, g.lc, Kab, g.Kc, 0, &fl);
-        g.gflops += (fl + 2.0 * gmap.size() * (2 * g.lc + 1)) * (double)g.ntasks;
         g.deriv.push_back(dv);
       }
   }
+  if (want_grad && *std::max_element(fadds.begin(), fadds.end()) >= kFixMaxAdds)
+    return dfail(LX3C_ENOTSUP, "gradient: an atom's force accumulator would take 2^32 or more contributions");
   if (want_grad) {
     std::vector<double> sph;
     p->sph_off.assign(9, 0);
@@ -649,7 +691,7 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
         }
     DCUDA(cudaMalloc(&p->d_jM, nm * 8));
     DCUDA(cudaMalloc(&p->d_jD, nd * 8));
-    DCUDA(cudaMalloc(&p->d_jY, nd * 16));
+    DCUDA(cudaMalloc(&p->d_jY, nd * kFixBytes));
     for (auto& g : p->groups)
       for (auto& L : g.L)
         if (L.jeng) {
@@ -660,9 +702,9 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
           }
         }
   }
-  DCUDA(cudaMalloc(&p->d_gacc, (size_t)p->naux_ao * 16));
-  DCUDA(cudaMalloc(&p->d_Jacc, (size_t)p->nao * p->nao * 16));
-  if (want_grad) DCUDA(cudaMalloc(&p->d_facc, (size_t)p->natom * 3 * 16));
+  DCUDA(cudaMalloc(&p->d_gacc, (size_t)p->naux_ao * kFixBytes));
+  DCUDA(cudaMalloc(&p->d_Jacc, (size_t)p->nao * p->nao * kFixBytes));
+  if (want_grad) DCUDA(cudaMalloc(&p->d_facc, (size_t)p->natom * 3 * kFixBytes));
   DCUDA(cudaStreamSynchronize(st));
   *out = p.release();
   return LX3C_OK;
@@ -672,8 +714,8 @@ lx3c_status lx3c_dfj_execute(lx3c_dfj* p, const double* D, const double* c, doub
   if (!p) return dfail(LX3C_EINVAL, "null plan");
   if (!D || !c || (!gamma && !J)) return dfail(LX3C_EINVAL, "null pointer");
   cudaStream_t st = (cudaStream_t)stream;
-  if (gamma) DCUDA(cudaMemsetAsync(p->d_gacc, 0, p->naux_ao * 16, st));
-  if (J) DCUDA(cudaMemsetAsync(p->d_Jacc, 0, p->nao * p->nao * 16, st));
+  if (gamma) DCUDA(cudaMemsetAsync(p->d_gacc, 0, p->naux_ao * kFixBytes, st));
+  if (J) DCUDA(cudaMemsetAsync(p->d_Jacc, 0, p->nao * p->nao * kFixBytes, st));
   for (auto& g : p->groups) {
     const long long np = (long long)g.counts.size(), na = (long long)g.auxs.size();
     DCUDA(launch_pair_precompute(p->orb->dev(), g.d_pairs, np, g.Ka, g.Kb, g.d_pairrec, g.d_pairab, st));
@@ -693,7 +735,7 @@ lx3c_status lx3c_dfj_execute(lx3c_dfj* p, const double* D, const double* c, doub
         dm.Jacc = d.Jacc;
         dm.ldD = d.ldD;
         dm.pair_ao = d.pair_ao;
-        if (J) DCUDA(cudaMemsetAsync(p->d_jY, 0, (size_t)d.nsub * d.nkrow * 16, st));
+        if (J) DCUDA(cudaMemsetAsync(p->d_jY, 0, (size_t)d.nsub * d.nkrow * kFixBytes, st));
         DCUDA(launch_jeng_matrix(dm, L.mgrid, st));
         if (gamma) DCUDA(launch_jeng_pair(dm, 0, st));
         DCUDA(launch_eri3c(d, L.grid, st));
@@ -772,7 +814,7 @@ lx3c_status lx3c_dfj_grad(lx3c_dfj* p, const double* D, const double* c, double*
   if (!p->gradient) return dfail(LX3C_EINVAL, "plan was built without gradient support (flags & 1)");
   if (!D || !c || !grad) return dfail(LX3C_EINVAL, "null pointer");
   cudaStream_t st = (cudaStream_t)stream;
-  DCUDA(cudaMemsetAsync(p->d_facc, 0, (size_t)p->natom * 3 * 16, st));
+  DCUDA(cudaMemsetAsync(p->d_facc, 0, (size_t)p->natom * 3 * kFixBytes, st));
   for (auto& g : p->groups) {
     const long long np = (long long)g.counts.size(), na = (long long)g.auxs.size();
     DCUDA(launch_aux_precompute(p->aux->dev(), g.d_auxs, na, g.Kc, g.d_auxrec, g.d_auxc, st));
@@ -917,12 +959,12 @@ struct lx3c_batch {
   int ndesc = 0;
   int smem = 0;
   int grid = 0;
-  // mode 1 splits the work items into shared-memory tiers, each run by a
-  // persistent kernel sized for the tier's largest item: items that fit two
-  // CTAs per SM, then the rest (one CTA per SM)
+  // mode 1 splits the work items into occupancy tiers, each run by a
+  // persistent kernel sized for the tier's largest item: items that fit three
+  // CTAs per SM (the 40-register kernel), then two, then the rest
   struct Tier {
     long long off = 0, n = 0;
-    int smem = 0, grid = 0;
+    int smem = 0, grid = 0, three = 0;
   };
   std::vector<Tier> tiers;
   cudaGraph_t graph = nullptr;        // mode 1: persistent kernels, one per tier
@@ -960,8 +1002,8 @@ cudaError_t capture_branches(lx3c_batch* b, const std::vector<ClassDesc>& descs,
     const int nmol = (int)b->mols.size();
     for (int m = 0; m < nmol; ++m) {
       lx3c_dfj* p = b->mols[m];
-      cudaMemsetAsync(p->d_gacc, 0, p->naux_ao * 16, cap);
-      cudaMemsetAsync(p->d_Jacc, 0, p->nao * p->nao * 16, cap);
+      cudaMemsetAsync(p->d_gacc, 0, p->naux_ao * kFixBytes, cap);
+      cudaMemsetAsync(p->d_Jacc, 0, p->nao * p->nao * kFixBytes, cap);
       for (auto& g : p->groups) {
         launch_pair_precompute(p->orb->dev(), g.d_pairs, (long long)g.counts.size(), g.Ka, g.Kb, g.d_pairrec,
                                g.d_pairab, cap);
@@ -1069,9 +1111,9 @@ lx3c_status lx3c_batch_plan(lx3c_batch** out, int nmol, const lx3c_basis* const*
     if (!tg) {
       long long mx = 0, mxa = 0;
       for (auto* p : b->mols) { mx = std::max(mx, p->nao); mxa = std::max(mxa, p->naux_ao); }
-      DCUDA(cudaMalloc(&tg, mxa * 16)); DCUDA(cudaMalloc(&tc, mxa * 8));
-      DCUDA(cudaMalloc(&tJ, mx * mx * 16)); DCUDA(cudaMalloc(&tD, mx * mx * 8));
-      DCUDA(cudaMemset(tg, 0, mxa * 16)); DCUDA(cudaMemset(tJ, 0, mx * mx * 16));
+      DCUDA(cudaMalloc(&tg, mxa * kFixBytes)); DCUDA(cudaMalloc(&tc, mxa * 8));
+      DCUDA(cudaMalloc(&tJ, mx * mx * kFixBytes)); DCUDA(cudaMalloc(&tD, mx * mx * 8));
+      DCUDA(cudaMemset(tg, 0, mxa * kFixBytes)); DCUDA(cudaMemset(tJ, 0, mx * mx * kFixBytes));
       DCUDA(cudaMemset(tc, 0, mxa * 8)); DCUDA(cudaMemset(tD, 0, mx * mx * 8));
     }
     DCUDA(launch_pair_precompute(owner->orb->dev(), g.d_pairs, (long long)g.counts.size(), g.Ka, g.Kb, g.d_pairrec,
@@ -1173,28 +1215,30 @@ lx3c_status lx3c_batch_bind(lx3c_batch* b, const double* const* D, const double*
     }
   }
   std::stable_sort(order.begin(), order.end(), [](auto& x, auto& y) { return x.first > y.first; });
-  // tiers: the items whose shared memory lets the persistent kernel keep two
-  // CTAs per SM, then the others; longest first within each tier
+  // tiers: the items whose shared memory lets the 40-register persistent
+  // kernel keep three CTAs per SM, then those that fit two CTAs of the
+  // unrestricted one, then the others; longest first within each tier
   std::vector<int2> work;
   b->tiers.clear();
-  for (int tier = 0; tier < 2; ++tier) {
+  auto tier_of = [&](int sm) { return persistent_occupancy(sm, 1) >= 3 ? 0 : (persistent_occupancy(sm, 0) >= 2 ? 1 : 2); };
+  for (int tier = 0; tier < 3; ++tier) {
     lx3c_batch::Tier T;
     T.off = (long long)work.size();
+    T.three = tier == 0 ? 1 : 0;
     for (auto& o : order) {
       const int sm = descs[o.second].smem_doubles * 8;
-      const bool two = persistent_occupancy(sm) >= 2;
-      if ((tier == 0) != two) continue;
+      if (tier_of(sm) != tier) continue;
       T.smem = std::max(T.smem, sm);
       for (long long t = 0; t < descs[o.second].ntiles; ++t) work.push_back(int2{o.second, (int)t});
     }
     T.n = (long long)work.size() - T.off;
     if (!T.n) continue;
-    T.grid = dev_nsm(b->ds) * persistent_occupancy(T.smem);
+    T.grid = dev_nsm(b->ds) * persistent_occupancy(T.smem, T.three);
     b->tiers.push_back(T);
   }
   cudaFree(b->d_descs);
   cudaFree(b->d_work);
-  if (!b->d_counter) DCUDA(cudaMalloc(&b->d_counter, 2 * sizeof(unsigned long long)));
+  if (!b->d_counter) DCUDA(cudaMalloc(&b->d_counter, 3 * sizeof(unsigned long long)));
   DCUDA(cudaMalloc(&b->d_descs, descs.size() * sizeof(ClassDesc)));
   DCUDA(cudaMalloc(&b->d_work, std::max<size_t>(work.size(), 1) * sizeof(int2)));
   DCUDA(cudaMemcpy(b->d_descs, descs.data(), descs.size() * sizeof(ClassDesc), cudaMemcpyHostToDevice));
@@ -1212,8 +1256,8 @@ lx3c_status lx3c_batch_bind(lx3c_batch* b, const double* const* D, const double*
   b->graph_kernels = 0;
   for (int m = 0; m < nmol; ++m) {
     lx3c_dfj* p = b->mols[m];
-    cudaMemsetAsync(p->d_gacc, 0, p->naux_ao * 16, cap);
-    cudaMemsetAsync(p->d_Jacc, 0, p->nao * p->nao * 16, cap);
+    cudaMemsetAsync(p->d_gacc, 0, p->naux_ao * kFixBytes, cap);
+    cudaMemsetAsync(p->d_Jacc, 0, p->nao * p->nao * kFixBytes, cap);
     for (auto& g : p->groups) {
       launch_pair_precompute(p->orb->dev(), g.d_pairs, (long long)g.counts.size(), g.Ka, g.Kb, g.d_pairrec,
                              g.d_pairab, cap);
@@ -1224,7 +1268,7 @@ lx3c_status lx3c_batch_bind(lx3c_batch* b, const double* const* D, const double*
   for (size_t t = 0; t < b->tiers.size(); ++t) {
     const auto& T = b->tiers[t];
     cudaMemsetAsync(b->d_counter + t, 0, sizeof(unsigned long long), cap);
-    launch_persistent(b->d_descs, b->d_work + T.off, T.n, b->d_counter + t, T.grid, T.smem, cap);
+    launch_persistent(b->d_descs, b->d_work + T.off, T.n, b->d_counter + t, T.grid, T.smem, T.three, cap);
     b->graph_kernels += 1;
   }
   for (int m = 0; m < nmol; ++m) {

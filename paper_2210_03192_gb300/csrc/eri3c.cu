@@ -705,7 +705,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
             const int2 e = __ldg(d.kent + q);
             v = fma(__ldg(d.pal + e.y), gq[t * ncc + e.x], v);
           }
-          fix_add(d.gacc + 2 * (__ldg(d.aux_ao + aux0 + t) + C), v);
+          fix_add(d.gacc + kFixWords * (__ldg(d.aux_ao + aux0 + t) + C), v);
         }
       }
       if (d.Jacc)
@@ -714,7 +714,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
                   const int t = (int)fc.div(r), c = r - t * ncc;
                   return fma(sm[BUF_T(gb, o * ncc + c, t)], Cp[r], acc);
                 },
-                [&](int o, double v) { fix_add(d.jY + 2 * (sub * nk + o), v); });
+                [&](int o, double v) { fix_add(d.jY + kFixWords * (sub * nk + o), v); });
       return;
     }
     // ---- ket: Cartesian -> solid harmonic.  With targets across lanes
@@ -821,6 +821,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       }
       __syncthreads();
       const int tatom = d.g_centre ? pat.y : pat.x;
+      double* tsum = part + T * 3 * nch;  // [tv][3]
       for (int w = tid; w < tv * 3; w += kThreads) {
         const int t = w / 3, ax = w - t * 3;
         double s0 = 0.0, s1 = 0.0;
@@ -831,8 +832,15 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
         }
         if (k < nch) s0 += part[(t * 3 + ax) * nch + k];
         const double s = s0 + s1;
-        fix_add(d.facc + 2 * (3 * tatom + ax), s);
-        fix_add(d.facc + 2 * (3 * __ldg(d.aux_atom + aux0 + t) + ax), -s);
+        tsum[w] = s;
+        fix_add(d.facc + kFixWords * (3 * __ldg(d.aux_atom + aux0 + t) + ax), -s);
+      }
+      __syncthreads();
+      // the pair's centre atom: the tile's kets summed first, one add per axis
+      if (tid < 3) {
+        double s = 0.0;
+        for (int t = 0; t < tv; ++t) s += tsum[t * 3 + tid];
+        fix_add(d.facc + kFixWords * (3 * tatom + tid), s);
       }
       return;
     }
@@ -937,7 +945,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
                 },
                 [&](int o, double v) {
                   const int t = (int)fC.div(o), C = o - t * nC;
-                  fix_add(d.gacc + 2 * (__ldg(d.aux_ao + aux0 + t) + C), wg * v);
+                  fix_add(d.gacc + kFixWords * (__ldg(d.aux_ao + aux0 + t) + C), wg * v);
                 });
       if (d.Jacc)
         seg_dot(nAB, tv * nC,
@@ -947,7 +955,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
                 },
                 [&](int o, double v) {
                   const int A = d.orient ? o % nA : o / nB, B = d.orient ? o / nA : o % nB;
-                  fix_add(d.Jacc + 2 * ((long long)(pao.x + A) * d.ldD + pao.y + B), wj * v);
+                  fix_add(d.Jacc + kFixWords * ((long long)(pao.x + A) * d.ldD + pao.y + B), wj * v);
                 });
       return;
     }
@@ -1060,9 +1068,9 @@ __global__ void jeng_finish_kernel(const __grid_constant__ ClassDesc d) {
   const double* M = d.jM + sub * (long long)nAB * nk;
   for (int s = lane; s < nAB; s += 32) {
     double v = 0.0;
-    for (int e = 0; e < nk; ++e) v = fma(M[s * nk + e], fix_decode(d.jY + 2 * (sub * nk + e)), v);
+    for (int e = 0; e < nk; ++e) v = fma(M[s * nk + e], fix_decode(d.jY + kFixWords * (sub * nk + e)), v);
     const int A = d.orient ? s % nA : s / nB, B = d.orient ? s / nA : s % nB;
-    fix_add(d.Jacc + 2 * ((long long)(pao.x + A) * d.ldD + pao.y + B), wj * v);
+    fix_add(d.Jacc + kFixWords * ((long long)(pao.x + A) * d.ldD + pao.y + B), wj * v);
   }
 }
 
@@ -1071,10 +1079,14 @@ __global__ void jeng_finish_kernel(const __grid_constant__ ClassDesc d) {
 // ordered longest first on the host).  No CTA ever waits on another.  The
 // item's descriptor is staged in shared memory (re-copied only when the class
 // changes), so the tile body reads its fields from there, not from global
-// memory.
-__global__ void __launch_bounds__(kThreads) eri3c_persistent(const ClassDesc* __restrict__ descs,
-                                                             const int2* __restrict__ work, long long nwork,
-                                                             unsigned long long* __restrict__ counter) {
+// memory.  kMinBlocks = 3 caps the registers at 40 so that three 512-thread
+// CTAs fit an SM (with a few spills to L1: the descriptor fields the
+// parameter-space form keeps in constant banks now live in registers);
+// kMinBlocks = 1 leaves the compiler free (64 registers, two CTAs per SM).
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) eri3c_persistent(const ClassDesc* __restrict__ descs,
+                                                                         const int2* __restrict__ work, long long nwork,
+                                                                         unsigned long long* __restrict__ counter) {
   extern __shared__ double sm[];
   __shared__ __align__(16) ClassDesc sd;
   __shared__ long long next;
@@ -1180,17 +1192,26 @@ cudaError_t launch_boys(const double* T, long long n, int mmax, const double* ta
 // The dynamic shared-memory attribute is set by persistent_occupancy(), which
 // callers run before any stream capture.
 cudaError_t launch_persistent(const ClassDesc* descs, const int2* work, long long nwork, unsigned long long* counter,
-                              int grid, int smem_bytes, cudaStream_t st) {
-  eri3c_persistent<<<grid, kThreads, smem_bytes, st>>>(descs, work, nwork, counter);
+                              int grid, int smem_bytes, int three, cudaStream_t st) {
+  if (three)
+    eri3c_persistent<3><<<grid, kThreads, smem_bytes, st>>>(descs, work, nwork, counter);
+  else
+    eri3c_persistent<1><<<grid, kThreads, smem_bytes, st>>>(descs, work, nwork, counter);
   return cudaGetLastError();
 }
 
-int persistent_occupancy(int smem_bytes) {
+int persistent_occupancy(int smem_bytes, int three) {
   int nb = 0;
-  cudaFuncSetAttribute(eri3c_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       232448 - (int)sizeof(ClassDesc) - 64);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eri3c_persistent, kThreads, smem_bytes) != cudaSuccess)
-    return 1;
+  const int cap = 232448 - (int)sizeof(ClassDesc) - 64;
+  cudaError_t e;
+  if (three) {
+    cudaFuncSetAttribute(eri3c_persistent<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eri3c_persistent<3>, kThreads, smem_bytes);
+  } else {
+    cudaFuncSetAttribute(eri3c_persistent<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eri3c_persistent<1>, kThreads, smem_bytes);
+  }
+  if (e != cudaSuccess) return 1;
   return nb < 1 ? 1 : nb;
 }
 
