@@ -194,6 +194,15 @@ lx3c_status lx3c_class_flops(int la, int lb, int lc, int Kab, int Kc, int bra_pu
  * Both return LX3C_EINVAL for arguments out of range.
  */
 lx3c_status lx3c_shape_hint(int la, int lb, int lc, int bra_pure, int kab, int kc, int ctas_per_sm);
+/*
+ * lx3c_tile_hint fixes the tile of later plans of that class (as oriented),
+ * kab and kc instead: T triples per tile (1..512) in chunks of G primitives
+ * (1..kab*kc; the planner balances G over the chunks).  It takes precedence
+ * over lx3c_shape_hint when the tile fits one CTA's shared memory, and is
+ * ignored otherwise.  T = 0 removes it.  Process-wide, thread-safe;
+ * LX3C_EINVAL for arguments out of range.
+ */
+lx3c_status lx3c_tile_hint(int la, int lb, int lc, int bra_pure, int kab, int kc, int T, int G);
 
 /*
  * HRR variant of class (la, lb | lc) as the planner orients it (Sec. 2.5.5):

@@ -24,7 +24,7 @@ from ._lib import LibraryError, check, ptr
 from . import workloads  # noqa: F401  (seeded input generators)
 
 __all__ = ["DeviceBasis", "Eri3cPlan", "DFJPlan", "DFJEnergy", "Batch", "MetricPlan", "cholesky", "cholesky_solve", "eri3c", "eri3c_host", "boys", "class_flops", "solid_harmonics",
-           "cvrr2_expansion", "LibraryError", "workloads"]
+           "cvrr2_expansion", "shape_hint", "tile_hint", "hrr_hint", "LibraryError", "workloads"]
 
 
 def _torch():
@@ -482,6 +482,13 @@ def shape_hint(la, lb, lc, kab, kc=1, ctas_per_sm=2, bra_pure=True):
     check(_lib.load().lx3c_shape_hint(la, lb, lc, int(bool(bra_pure)), kab, kc, ctas_per_sm), "lx3c_shape_hint")
 
 
+def tile_hint(la, lb, lc, kab, kc, T, G, bra_pure=True):
+    """Fix the tile of later plans of class (la, lb | lc) with kab x kc
+    primitives: T triples per tile, chunks of G primitives (lx3c_tile_hint;
+    T = 0 removes the hint)."""
+    check(_lib.load().lx3c_tile_hint(la, lb, lc, int(bool(bra_pure)), kab, kc, int(T), int(G)), "lx3c_tile_hint")
+
+
 def hrr_hint(la, lb, lc, variant, bra_pure=True):
     """HRR variant of class (la, lb | lc) for later plans: 0 one quantum per
     round, 1 two quanta per round, -1 remove the hint (lx3c_hrr_hint)."""
@@ -512,16 +519,22 @@ HINTS_GB300 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "shape_hi
 
 
 def load_shape_hints(path=HINTS_GB300):
-    """Apply a tuned hints file ("la lb lc bra_pure kab kc ctas_per_sm" per line,
-    '#' comments); returns the number of hints applied."""
+    """Apply a tuned hints file, '#' comments; per line either
+    "la lb lc bra_pure kab kc ctas_per_sm" (lx3c_shape_hint) or
+    "la lb lc bra_pure kab kc 0 T G" (lx3c_tile_hint); returns the number of
+    hints applied."""
     n = 0
     with open(path) as f:
         for line in f:
             line = line.split("#", 1)[0].split()
             if not line:
                 continue
-            la, lb, lc, pure, kab, kc, ctas = (int(x) for x in line)
-            shape_hint(la, lb, lc, kab, kc, ctas, bool(pure))
+            v = [int(x) for x in line]
+            la, lb, lc, pure, kab, kc, ctas = v[:7]
+            if len(v) == 9:
+                tile_hint(la, lb, lc, kab, kc, v[7], v[8], bool(pure))
+            else:
+                shape_hint(la, lb, lc, kab, kc, ctas, bool(pure))
             n += 1
     return n
 

@@ -78,6 +78,7 @@ EXPORTS = {
     "lx3c_cvrr2_expansion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "lx3c_shape_hint": (ctypes.c_int, [ctypes.c_int] * 7),
+    "lx3c_tile_hint": (ctypes.c_int, [ctypes.c_int] * 8),
     "lx3c_hrr_hint": (ctypes.c_int, [ctypes.c_int] * 5),
     "lx3c_hrr_tables_check": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.c_void_p, c_f64p]),
     "lx3c_set_orientation_threshold": (ctypes.c_int, [ctypes.c_double]),

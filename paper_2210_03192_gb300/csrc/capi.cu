@@ -746,6 +746,14 @@ lx3c_status lx3c_shape_hint(int la, int lb, int lc, int bra_pure, int kab, int k
   return LX3C_OK;
 }
 
+lx3c_status lx3c_tile_hint(int la, int lb, int lc, int bra_pure, int kab, int kc, int T, int G) {
+  if (la < 0 || lb < 0 || lc < 0 || la > LX3C_LMAX_ORB + 1 || lb > LX3C_LMAX_ORB + 1 || lc > LX3C_LMAX_AUX ||
+      kab < 1 || kc < 1 || T < 0 || T > 512 || (T > 0 && (G < 1 || G > kab * kc)))
+    return fail(LX3C_EINVAL, "tile_hint: bad argument");
+  set_tile_hint(la, lb, lc, bra_pure, kab, kc, T, G);
+  return LX3C_OK;
+}
+
 lx3c_status lx3c_shape_query(int la, int lb, int lc, int bra_pure, int kab, int kc, int64_t naux, int ctas_per_sm,
                              int32_t* out) {
   if (!out || la < 0 || lb < 0 || lc < 0 || la > LX3C_LMAX_ORB + 1 || lb > LX3C_LMAX_ORB + 1 ||

@@ -284,6 +284,7 @@ double hrr_moment_error(const ClassTables& ct, const double AB[3]);
 LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit);
 LaunchShape choose_shape_for(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit, int ctas);
 void set_shape_hint(int la, int lb, int lc, int bra_pure, int Kab, int Kc, int ctas);
+void set_tile_hint(int la, int lb, int lc, int bra_pure, int Kab, int Kc, int T, int G);
 void fill_layout(ClassDesc& d, const ClassTables& ct, const LaunchShape& s);
 
 // Process-wide accuracy settings (capi.cu): the orientation split's

@@ -753,6 +753,39 @@ int shape_hint(const ClassTables& ct, int Kab, int Kc) {
   return it == g_hints.end() ? 0 : it->second;
 }
 
+namespace {
+std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> g_tile_hints;  // -> (T, G)
+}  // namespace
+
+void set_tile_hint(int la, int lb, int lc, int bra_pure, int Kab, int Kc, int T, int G) {
+  std::lock_guard<std::mutex> lk(g_hint_mu);
+  auto key = std::make_tuple(la, lb, lc, bra_pure ? 1 : 0, Kab, Kc);
+  if (T <= 0) g_tile_hints.erase(key); else g_tile_hints[key] = {T, G};
+}
+
+// The hinted tile (T triples, chunks of G primitives, G balanced over the
+// chunks) when one is set for the class and it fits one CTA per SM;
+// smem_bytes = -1 otherwise.
+LaunchShape tile_hint_shape(const ClassTables& ct, int Kab, int Kc, int smem_limit) {
+  std::pair<int, int> h{0, 0};
+  {
+    std::lock_guard<std::mutex> lk(g_hint_mu);
+    auto it = g_tile_hints.find(std::make_tuple(ct.la, ct.lb, ct.lc, ct.bra_pure ? 1 : 0, Kab, Kc));
+    if (it != g_tile_hints.end()) h = it->second;
+  }
+  LaunchShape sh{1, 1, 1, -1};
+  if (h.first <= 0) return sh;
+  const int K = Kab * Kc, T = h.first;
+  int G = std::max(1, std::min(h.second, K));
+  const int nch = (K + G - 1) / G;
+  G = (K + nch - 1) / nch;
+  const int mode = T >= 32 ? 0 : 1;
+  Sizes s;
+  buffer_sizes(ct, Kab, Kc, T, G, mode, s, nullptr);
+  if (s.total * 8 > (long long)smem_limit - 1024) return sh;
+  return LaunchShape{T, G, mode, (int)(s.total * 8)};
+}
+
 // Largest T (then largest balanced G) whose tile fits `ctas` CTAs per SM,
 // falling back to fewer CTAs per SM when nothing fits.
 LaunchShape choose_shape_for(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit, int ctas) {
@@ -791,9 +824,12 @@ LaunchShape choose_shape_for(const ClassTables& ct, int Kab, int Kc, long long n
   return best;
 }
 
-// The planner's shape: two CTAs per SM unless a tuned hint for this class,
-// contraction and ket contraction says otherwise.
+// The planner's shape: a tuned tile hint (T, G) for this class, contraction
+// and ket contraction when one is set and fits; else two CTAs per SM unless
+// a tuned CTAs-per-SM hint says otherwise.
 LaunchShape choose_shape(const ClassTables& ct, int Kab, int Kc, long long naux, int smem_limit) {
+  const LaunchShape th = tile_hint_shape(ct, Kab, Kc, smem_limit);
+  if (th.smem_bytes >= 0) return th;
   const int h = shape_hint(ct, Kab, Kc);
   return choose_shape_for(ct, Kab, Kc, naux, smem_limit, h > 0 ? h : 2);
 }

@@ -157,6 +157,45 @@ def test_shape_query_budgets_and_hints(tmp_path):
         lx.shape_query(9, 4, 1, 36, 1, 512, 2)
 
 
+
+def test_tile_hints_fix_the_tile_and_take_precedence(tmp_path):
+    """A tile hint fixes (T, G) of exactly its class (G balanced over the
+    chunks), wins over a CTAs-per-SM hint, is ignored when the tile cannot fit
+    one CTA's shared memory, and rejects arguments out of range."""
+    L = _lib.load()
+    default = lx.shape_query(0, 0, 6, 36, 1, 512)
+    lx.shape_hint(0, 0, 6, 36, 1, 3)
+    lx.tile_hint(0, 0, 6, 36, 1, 16, 8)
+    try:
+        T, G, mode, sb = lx.shape_query(0, 0, 6, 36, 1, 512)
+        # 36 primitives in chunks of at most 8: five chunks, balanced to 8 (8+8+8+8+4)
+        assert (T, G, mode) == (16, 8, 1) and 0 < sb <= 233472 - 1024
+        lx.tile_hint(0, 0, 6, 36, 1, 4, 36)
+        assert lx.shape_query(0, 0, 6, 36, 1, 512)[:3] == (4, 36, 1)
+        lx.tile_hint(0, 0, 6, 36, 1, 32, 12)  # 36 in chunks of 12: three chunks of 12
+        assert lx.shape_query(0, 0, 6, 36, 1, 512)[:3] == (32, 12, 0)
+        assert lx.shape_query(0, 0, 6, 9, 1, 512) == lx.shape_query(0, 0, 6, 9, 1, 512, 2)  # other kab untouched
+        lx.tile_hint(4, 4, 6, 36, 1, 512, 36)  # far beyond one CTA's shared memory: ignored
+        assert lx.shape_query(4, 4, 6, 36, 1, 512) == lx.shape_query(4, 4, 6, 36, 1, 512, 2)
+    finally:
+        lx.tile_hint(0, 0, 6, 36, 1, 0, 0)
+        lx.tile_hint(4, 4, 6, 36, 1, 0, 0)
+        lx.shape_hint(0, 0, 6, 36, 1, 0)
+    assert lx.shape_query(0, 0, 6, 36, 1, 512) == default
+    assert L.lx3c_tile_hint(0, 0, 6, 1, 36, 1, 513, 1) == -1
+    assert L.lx3c_tile_hint(0, 0, 6, 1, 36, 1, 16, 37) == -1
+    assert L.lx3c_tile_hint(0, 0, 6, 1, 36, 1, 16, 0) == -1
+    assert L.lx3c_tile_hint(0, 0, 9, 1, 36, 1, 16, 8) == -1
+    f = tmp_path / "tiles.txt"
+    f.write_text("# la lb lc pure kab kc 0 T G\n0 0 6 1 36 1 0 8 18\n0 0 5 1 36 1 3\n")
+    assert lx.load_shape_hints(str(f)) == 2
+    try:
+        assert lx.shape_query(0, 0, 6, 36, 1, 512)[:2] == (8, 18)
+        assert lx.shape_query(0, 0, 5, 36, 1, 512) == lx.shape_query(0, 0, 5, 36, 1, 512, 3)
+    finally:
+        lx.tile_hint(0, 0, 6, 36, 1, 0, 0)
+        lx.shape_hint(0, 0, 5, 36, 1, 0)
+
 def test_committed_shape_hints_file():
     """The shipped GB300 hints: every line a valid class with a 1-3 CTA target,
     loadable, and each hinted shape fits the shared memory of its target."""
