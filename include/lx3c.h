@@ -286,8 +286,10 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  *   (AB|C) = sum_e M[AB][e] (e 0|C)) is formed once per pair; per triple
  *   gamma_P = sum_c T_Cc sum_e (M^T D)_e (e 0|c) and y_e += sum_c (e 0|c)
  *   (T^T c_P)_c, then J_AB += M y per pair -- no ket transform, HRR or bra
- *   transform per triple.  Launches whose bra map does not fit in shared
- *   memory keep the per-integral digestion.  Same results to rounding.
+ *   transform per triple.  A launch keeps the per-integral digestion when its
+ *   bra map does not fit in shared memory, or when the contracted form would
+ *   take more flops (few kets per pair: the per-pair bra maps cost more than
+ *   the per-triple stages they replace).  Same results to rounding.
  *   Screening: a (pair, ket) triple is kept when Q_ab Q_P >= schwarz_tol, with
  *   Q_ab = 20 sum over primitive pairs of |c_a c_b| exp(-za zb/g AB^2)
  *   sqrt(2 pi^{5/2}/(g^2 sqrt(2g))) (|PA|^2+1/(2g))^{la/2} (|PB|^2+1/(2g))^{lb/2}

@@ -521,27 +521,33 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
             dj.smem_doubles += (int)need;
           }
         }
-        if ((long long)dm.smem_doubles * 8 <= 232448 && (long long)dj.smem_doubles * 8 <= 232448) {
+        // flops: per triple the primitive loop, the gather and the two
+        // contractions over (e, c) (plus gamma's ket transform); per sub-pair
+        // the bra map (the HRR and bra stages at nC = nkrow) and two GEMVs
+        const double gather = 2.0 * ct->gterm.size(), ket = 2.0 * ct->kent.size() * ct->nkrow;
+        const double hrrbra = (ct->flops_contr - gather - ket) / ct->nC * ct->nkrow;
+        const double nab = (double)d.onA * d.onB, nk = ct->nkrow;
+        double tris = 0, primtris = 0;
+        for (auto& sp : sub[o]) {
+          tris += g.counts[sp.x];
+          primtris += (double)g.counts[sp.x] * sp.z * g.Kc;
+        }
+        const double jflops = primtris * ct->flops_prim + tris * (gather + 4.0 * nk * ct->ncc + 2.0 * ct->kent.size()) +
+                              (double)d.nsub * (hrrbra + 4.0 * nab * nk);
+        // the same triples digested per integral (what the plain path counts)
+        const double pflops = primtris * ct->flops_prim + tris * (ct->flops_contr + 4.0 * nab * ct->nC);
+        // contract the launch only where that saves work: with few kets per
+        // pair the per-pair bra maps cost more than the per-triple stages
+        // they replace
+        if ((long long)dm.smem_doubles * 8 <= 232448 && (long long)dj.smem_doubles * 8 <= 232448 &&
+            jflops < pflops) {
           dm.npair = np; dm.naux = na; dm.nsub = d.nsub; dm.subpairs = d.subpairs; dm.pairab = g.d_pairab;
           L.jeng = true;
           L.mdesc = dm;
           L.jdesc = dj;
           L.mgrid = (int)std::min<long long>(d.nsub, (long long)dev_nsm(ds) * 4);
-          // flops: per triple the primitive loop, the gather and the two
-          // contractions over (e, c) (plus gamma's ket transform); per sub-pair
-          // the bra map (the HRR and bra stages at nC = nkrow) and two GEMVs
-          const double gather = 2.0 * ct->gterm.size(), ket = 2.0 * ct->kent.size() * ct->nkrow;
-          const double hrrbra = (ct->flops_contr - gather - ket) / ct->nC * ct->nkrow;
-          const double nab = (double)d.onA * d.onB, nk = ct->nkrow;
-          double tris = 0, primtris = 0;
-          for (auto& sp : sub[o]) {
-            tris += g.counts[sp.x];
-            primtris += (double)g.counts[sp.x] * sp.z * g.Kc;
-          }
-          L.jflops = primtris * ct->flops_prim + tris * (gather + 4.0 * nk * ct->ncc + 2.0 * ct->kent.size()) +
-                     (double)d.nsub * (hrrbra + 4.0 * nab * nk);
-          // the same triples digested per integral (what the plain path counts)
-          L.pflops = primtris * ct->flops_prim + tris * (ct->flops_contr + 4.0 * nab * ct->nC);
+          L.jflops = jflops;
+          L.pflops = pflops;
           p->contract = true;
         }
       }

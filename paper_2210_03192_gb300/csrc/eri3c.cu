@@ -391,12 +391,13 @@ __device__ __forceinline__ Buf hrr_and_bra(const ClassDesc& d, double* sm, int T
 }
 
 // One tile: (sub-pair, up to T ket shells) through every stage, ending in the
-// store, the DF-J digestion or the gradient digestion.  kMulti instantiates
-// the several-density digestion on tensor-core tiles (digest == 4) and the
-// contraction at the (e 0|c) level (digest == 5) in a kernel of its own, so
-// that the other launches keep the lower register count of the plain
-// instantiation.
-template <bool kMulti>
+// store, the DF-J digestion or the gradient digestion.  kVar selects the
+// instantiation: 0 the plain kernel (store, per-integral DF-J and gradient
+// digestion), 1 adds the several-density digestion on FP64 tensor-core
+// tiles (digest == 4), 2 the contraction at the (e 0|c) level (digest ==
+// 5), each in a kernel of its own so that the plain launches keep their
+// register count.
+template <int kVar>
 __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, double* sm) {
   const unsigned tid = threadIdx.x;
   const int T = d.T, G = d.G, mode = d.mode, lc = d.lc, Lab = d.Lab;
@@ -658,7 +659,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       }
     }
     __syncthreads();
-    if (kMulti && d.digest == 5) {
+    if (kVar == 2 && d.digest == 5) {
       // ---- DF-J contracted at the (e 0|c) level (the analogue of a
       // J-engine: D and c meet the intermediates, not the integrals).  With
       // the pair's bra map M (HRR then bra transforms, (AB|C) = sum_e
@@ -844,7 +845,7 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
       }
       return;
     }
-    if (kMulti && d.digest == 4) {
+    if (kVar == 1 && d.digest == 4) {
       // ---- DF-J digestion for nd <= 8 densities at once, as two small GEMMs
       // on FP64 tensor-core tiles (m8n8k4), with M rows per warp tile:
       //   gamma[d][t][C] = wg * sum_s I[t][s][C] Ds[s][d]    (M = tv*nC, K = nAB)
@@ -989,14 +990,20 @@ __device__ __forceinline__ void tile_body(const ClassDesc& d, long long tile, do
 // One class launch: CTAs stride over the class's tiles.
 __global__ void __launch_bounds__(kThreads) eri3c_kernel(const __grid_constant__ ClassDesc d) {
   extern __shared__ double sm[];
-  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body<false>(d, tile, sm);
+  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body<0>(d, tile, sm);
 }
 
-// The same for DF-J launches digesting several densities (digest == 4) or
-// contracting at the (e 0|c) level (digest == 5).
+// The same for DF-J launches digesting several densities (digest == 4).
 __global__ void __launch_bounds__(kThreads) eri3c_multi_kernel(const __grid_constant__ ClassDesc d) {
   extern __shared__ double sm[];
-  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body<true>(d, tile, sm);
+  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body<1>(d, tile, sm);
+}
+
+// DF-J launches contracting at the (e 0|c) level (digest == 5), at the
+// plain kernel's three CTAs per SM.
+__global__ void __launch_bounds__(kThreads, 3) eri3c_contract_kernel(const __grid_constant__ ClassDesc d) {
+  extern __shared__ double sm[];
+  for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body<2>(d, tile, sm);
 }
 
 // The bra map M of every sub-pair of a launch (digest 5): HRR and bra
@@ -1107,7 +1114,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) eri3c_persistent(const C
       cur = wk.x;
       __syncthreads();
     }
-    tile_body<false>(sd, wk.y, sm);
+    tile_body<0>(sd, wk.y, sm);
   }
 }
 
@@ -1151,10 +1158,14 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(eri3c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(eri3c_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(eri3c_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (d.digest >= 4)
+  if (d.digest == 5)
+    eri3c_contract_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);
+  else if (d.digest == 4)
     eri3c_multi_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);
   else
     eri3c_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);

@@ -15,9 +15,10 @@ classes alike) when its best candidate beats the default by more than
 
 Classes: every (la, lb | lc) with (K_a, K_b) pairs of the DF-J and batch
 orbital recipes (s K=6, p K=3, d/f/g K=1) and of the sweep (K_a = K_b in
-{3, 6}), la + lb <= 4, kab >= 3.
+{3, 6}), la + lb <= --lmax-ab (default 3), kab >= 3, heaviest contraction
+first; tuning stops after --budget seconds.
 
-    python -m paper_2210_03192_gb300.tune_tiles [--out FILE] [--npair N] [--append]
+    python -m paper_2210_03192_gb300.tune_tiles [--out FILE] [--npair N] [--budget S] [--append]
 """
 import argparse
 import time
@@ -26,12 +27,12 @@ TS = (1, 2, 4, 8, 16, 32, 64, 128, 256)
 GS = (1, 2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 32, 36)
 
 
-def class_list():
+def class_list(lmax_ab=3):
     ks = {0: 6, 1: 3, 2: 1, 3: 1, 4: 1}
     out = set()
     for la in range(5):
         for lb in range(5):
-            if la + lb > 4:
+            if la + lb > lmax_ab:
                 continue
             pairs = {(ks[la], ks[lb])}
             pairs |= {(3, 3), (6, 6)}
@@ -40,14 +41,16 @@ def class_list():
                     continue
                 for lc in range(7):
                     out.add((la, lb, lc, ka, kb))
-    return sorted(out)
+    return sorted(out, key=lambda c: (-c[3] * c[4], c[0] + c[1], c))
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None, help="hints file to write")
     ap.add_argument("--append", action="store_true", help="append to --out instead of overwriting")
-    ap.add_argument("--npair", type=int, default=1024)
+    ap.add_argument("--npair", type=int, default=256)
+    ap.add_argument("--budget", type=float, default=600.0, help="stop after this many seconds")
+    ap.add_argument("--lmax-ab", type=int, default=3)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--margin", type=float, default=0.03)
     ap.add_argument("--classes", nargs="*", default=None, help="subset la,lb,lc,Ka,Kb")
@@ -56,7 +59,7 @@ def main(argv=None):
     import paper_2210_03192_gb300 as lx
     from paper_2210_03192_gb300 import workloads as W
 
-    classes = class_list()
+    classes = class_list(args.lmax_ab)
     if args.classes:
         classes = [tuple(int(x) for x in c.split(",")) for c in args.classes]
 
@@ -76,7 +79,11 @@ def main(argv=None):
         return best, shape
 
     lines, t0 = [], time.time()
+    done = 0
     for (la, lb, lc, ka, kb) in classes:
+        if time.time() - t0 > args.budget:
+            break
+        done += 1
         kab = ka * kb
         p = W.class_problem(la, lb, lc, args.npair, 512, Ka=ka, Kb=kb, Kc=1, box=20.0, exp_lo=0.05, exp_hi=1.0e4)
         orb, aux = lx.DeviceBasis(p.orb), lx.DeviceBasis(p.aux)
@@ -110,7 +117,7 @@ def main(argv=None):
     if args.out:
         with open(args.out, "a" if args.append else "w") as f:
             f.write(text)
-    print("tuned %d classes in %.0f s, %d hint lines" % (len(classes), time.time() - t0, len(set(lines))))
+    print("tuned %d of %d classes in %.0f s, %d hint lines" % (done, len(classes), time.time() - t0, len(set(lines))))
 
 
 if __name__ == "__main__":

@@ -124,7 +124,8 @@ def test_dfj_contracted_at_intermediates(lx, shape, recipe_aux):
     Dt, ct = torch.tensor(D, device="cuda"), torch.tensor(c, device="cuda")
     plain = lx.DFJPlan(cl.orb, cl.aux, 1e-12)
     jeng = lx.DFJPlan(cl.orb, cl.aux, 1e-12, contract=True)
-    assert jeng.ntasks == plain.ntasks and jeng.flops < plain.flops
+    # launches contract only where that saves flops
+    assert jeng.ntasks == plain.ntasks and jeng.flops <= plain.flops
     g0, J0 = plain.execute(Dt, ct)
     g1, J1 = jeng.execute(Dt, ct)
     g0, J0, g1, J1 = (x.cpu().numpy() for x in (g0, J0, g1, J1))

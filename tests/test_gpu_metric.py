@@ -2,9 +2,9 @@
 factor, the solve c = V^{-1} gamma and the one-call DF-J Coulomb build
 (Sec. 1 and Sec. 4: density fitting of the Coulomb operator).
 
-V is compared element by element with the oracle (1e-12 relative or 1e-14
-absolute, else 1e-12 of its shell-pair block's largest element, against the
-binary128 oracle).  The factor and the solve are compared with numpy's on the
+V is compared element by element with the binary128 oracle (1e-12 relative
+or 1e-14 absolute, else 1e-12 of its shell-pair block's largest element plus
+1e-14 of the block's Cauchy-Schwarz scale, see blocks_ok).  The factor and the solve are compared with numpy's on the
 same matrices; their forward error is bounded by the condition number, so
 those tolerances carry kappa(V) explicitly.
 """
@@ -29,14 +29,24 @@ def lx():
 
 
 def blocks_ok(G, O, aux):
+    """Per element 1e-12 relative or 1e-14 absolute; else within
+    1e-12 max|block| + 1e-14 S_PQ, with S_PQ = sqrt(max (P|P) max (Q|Q)) the
+    block's Cauchy-Schwarz scale.  The primitives are not normalised (their
+    coefficients are used as given), so an absolute 1e-14 means nothing by
+    itself: S_PQ puts it at the scale of the two functions, where it is the
+    1e-14 of unit-normalised ones.  It decides blocks that vanish, or nearly,
+    by symmetry (same-centre pairs with l_P != l_Q are exactly zero), whose
+    computed values are the rounding of intermediates of size S_PQ."""
     aq = oracle.ao_offsets(aux)
     err = np.abs(G - O)
+    dg = np.diag(O)
     strict = err <= np.maximum(1e-12 * np.abs(O), 1e-14)
     ok = strict.copy()
     for i in range(aux.nshell):
         for j in range(aux.nshell):
             s = (slice(aq[i], aq[i + 1]), slice(aq[j], aq[j + 1]))
-            ok[s] |= err[s] <= 1e-12 * np.abs(O[s]).max() + 1e-14
+            spq = np.sqrt(dg[aq[i]:aq[i + 1]].max() * dg[aq[j]:aq[j + 1]].max())
+            ok[s] |= err[s] <= 1e-12 * np.abs(O[s]).max() + 1e-14 * spq
     return ok
 
 
