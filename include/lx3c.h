@@ -123,11 +123,9 @@ lx3c_status lx3c_plan_sizes(const lx3c_plan* plan, int64_t* block, int64_t* tota
  * per ket shell, its contracted stages (a pair split across the two
  * orientations pays the contracted stages twice)].
  *
- * Orientation: a pair runs in one orientation when one of them keeps the
- * weighted HRR amplification within the threshold (lx3c_set_orientation_
- * threshold): the cheaper one (the HRR moving the lower angular momentum)
- * when it qualifies, else the other; for la == lb the one with the smaller
- * amplification.  Otherwise its primitive pairs are split by compact centre.
+ * Orientation: a pair runs in the orientation with the smaller weighted HRR
+ * amplification when that is within the threshold (lx3c_set_orientation_
+ * threshold); otherwise its primitive pairs are split by compact centre.
  */
 lx3c_status lx3c_plan_info(const lx3c_plan* plan, int64_t* out, int n);
 

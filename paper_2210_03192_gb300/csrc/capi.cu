@@ -222,11 +222,13 @@ namespace lx3c {
 //   amp = ((|AB| + s) / (|P - target| + s))^l_target,  s = 1/sqrt(2 gamma),
 // weighted by the primitive pair's share of the largest prefactor
 // |c_a c_b exp(-za zb/gamma AB^2)/gamma| in the pair.  A pair keeps one
-// orientation when one has its worst weighted amp at most kAmpMax: the one
-// with fewer flops (HRR moving the lower angular momentum) when it qualifies,
-// for la == lb the one with the smaller amp.  Otherwise every primitive pair
-// runs on its more compact centre (two launches, the second accumulating
-// transposed).  Without HRR (lb = 0) the caller's orientation is always kept.
+// orientation (the one with the smaller worst weighted amp) when that worst
+// amp is at most kAmpMax; otherwise every primitive pair runs on its more
+// compact centre (two launches, the second accumulating transposed).
+// Without HRR (lb = 0) the caller's orientation is always kept.  (Preferring
+// the orientation with fewer flops whenever its amp is within kAmpMax saves
+// flops only on pairs whose cheaper side amplifies 5-300x, and those pairs
+// then miss 1e-12: the smaller amplification wins.)
 namespace {
 std::atomic<double> g_amp_max{kDefaultAmpMax};
 std::atomic<int> g_comp_bits{0};
@@ -235,17 +237,8 @@ std::atomic<int> g_comp_bits{0};
 double orientation_amp_max() { return g_amp_max.load(); }
 int compensation_bits() { return g_comp_bits.load(); }
 
-int cheaper_orientation(int la, int lb, int lc, int bra_pure, int Kab, int Kc) {
-  if (lb == 0) return 0;
-  if (la == lb) return -1;
-  const ClassTables& a = class_tables(la, lb, lc, bra_pure);
-  const ClassTables& b = class_tables(lb, la, lc, bra_pure);
-  const double ca = a.flops_prim * Kab * Kc + a.flops_contr, cb = b.flops_prim * Kab * Kc + b.flops_contr;
-  return cb < ca ? 1 : 0;
-}
-
 void split_orientation(const lx3c_basis* orb, int a, int b, int la, int lb, std::vector<int>& primA,
-                       std::vector<int>& primB, int prefer) {
+                       std::vector<int>& primB) {
   const double kAmpMax = orientation_amp_max();
   const int Ka = orb->k[a], Kb = orb->k[b];
   const double* A = &orb->xyz[3 * a];
@@ -273,18 +266,10 @@ void split_orientation(const lx3c_basis* orb, int a, int b, int la, int lb, std:
     worstB = std::max(worstB, ampB[r] * f);
   }
   // one orientation for the whole pair when one is within the threshold:
-  // the cheaper one if it is, else the other; with equal costs the one with
-  // the smaller amplification
+  // the one with the smaller amplification
   int whole = -1;
-  if (lb == 0) {
-    whole = 0;
-  } else if (prefer < 0) {
-    if (std::min(worstA, worstB) <= kAmpMax) whole = worstB < worstA ? 1 : 0;
-  } else {
-    const double wp = prefer ? worstB : worstA, wo = prefer ? worstA : worstB;
-    if (wp <= kAmpMax) whole = prefer;
-    else if (wo <= kAmpMax) whole = 1 - prefer;
-  }
+  if (lb == 0) whole = 0;
+  else if (std::min(worstA, worstB) <= kAmpMax) whole = worstB < worstA ? 1 : 0;
   for (int ia = 0; ia < Ka; ++ia)
     for (int ib = 0; ib < Kb; ++ib) {
       const bool onB = whole >= 0 ? whole == 1 : orb->exps[orb->off[b] + ib] > orb->exps[orb->off[a] + ia];
@@ -506,10 +491,9 @@ lx3c_status lx3c_eri3c_plan(lx3c_plan** out, const lx3c_basis* orb, const lx3c_b
   std::vector<int4> subA, subB;
   std::vector<int> primA, primB;
   int kA = 0, kB = 0;
-  const int prefer = cheaper_orientation(la, lb, lc, p->bra_pure, Ka * Kb, Kc);
   for (int64_t i = 0; i < npair; ++i) {
     int oa = (int)primA.size(), ob = (int)primB.size();
-    split_orientation(orb, pairs[2 * i], pairs[2 * i + 1], la, lb, primA, primB, prefer);
+    split_orientation(orb, pairs[2 * i], pairs[2 * i + 1], la, lb, primA, primB);
     int na = (int)primA.size() - oa, nb = (int)primB.size() - ob;
     if (na) subA.push_back(int4{(int)i, oa, na, 0});
     if (nb) subB.push_back(int4{(int)i, ob, nb, na > 0 ? 1 : 0});

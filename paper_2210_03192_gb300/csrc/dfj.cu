@@ -408,15 +408,9 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
     std::vector<int4> sub[2];
     std::vector<int> prim[2];
     int kmax[2] = {0, 0}, cmax = 0;
-    int prefer;
-    try {
-      prefer = cheaper_orientation(g.la, g.lb, g.lc, 1, g.Ka * g.Kb, g.Kc);
-    } catch (std::exception& e) {
-      return dfail(LX3C_ENOTSUP, e.what());
-    }
     for (long long i = 0; i < np; ++i) {
       int oa = (int)prim[0].size(), ob = (int)prim[1].size();
-      split_orientation(orb, g.pairs[2 * i], g.pairs[2 * i + 1], g.la, g.lb, prim[0], prim[1], prefer);
+      split_orientation(orb, g.pairs[2 * i], g.pairs[2 * i + 1], g.la, g.lb, prim[0], prim[1]);
       int na_ = (int)prim[0].size() - oa, nb_ = (int)prim[1].size() - ob;
       if (na_) sub[0].push_back(int4{(int)i, oa, na_, 0});
       if (nb_) sub[1].push_back(int4{(int)i, ob, nb_, 0});
@@ -578,15 +572,9 @@ lx3c_status lx3c_dfj_plan(lx3c_dfj** out, const lx3c_basis* orb, const lx3c_basi
         std::vector<int4> dsub[2];
         std::vector<int> dprim[2];
         int dk[2] = {0, 0};
-        int dprefer;
-        try {
-          dprefer = cheaper_orientation(l1, l2, g.lc, 0, Kab, g.Kc);
-        } catch (std::exception& e) {
-          return dfail(LX3C_ENOTSUP, e.what());
-        }
         for (long long i = 0; i < np; ++i) {
           int oa = (int)dprim[0].size(), ob = (int)dprim[1].size();
-          split_orientation(orb, g.pairs[2 * i], g.pairs[2 * i + 1], l1, l2, dprim[0], dprim[1], dprefer);
+          split_orientation(orb, g.pairs[2 * i], g.pairs[2 * i + 1], l1, l2, dprim[0], dprim[1]);
           int na_ = (int)dprim[0].size() - oa, nb_ = (int)dprim[1].size() - ob;
           if (na_) dsub[0].push_back(int4{(int)i, oa, na_, 0});
           if (nb_) dsub[1].push_back(int4{(int)i, ob, nb_, 0});

@@ -312,15 +312,9 @@ namespace lx3c {
 // Allocate and fill the device copy of a basis from its host vectors
 // (synchronises st).  No validation: callers check the shell table first.
 int basis_upload(lx3c_basis* b, cudaStream_t st);
-// Orientation of a class's pairs.  cheaper_orientation: 0 when the
-// recurrences on A cost fewer flops at (Kab, Kc) than those on B, 1 when B's
-// do, -1 when the two cost the same (la == lb).  split_orientation appends
-// the pair's primitive pairs to primA or primB: the whole pair goes to the
-// preferred orientation when its weighted HRR amplification is at most the
-// orientation threshold, else to the other one when that one's is; with
-// prefer = -1 to the one with the smaller amplification; otherwise every
-// primitive pair runs on its more compact centre.
-int cheaper_orientation(int la, int lb, int lc, int bra_pure, int Kab, int Kc);
+// Orientation of a pair: its primitive pairs go to primA or primB -- all to
+// the orientation with the smaller weighted HRR amplification when that is
+// at most the orientation threshold, else each to its more compact centre.
 void split_orientation(const lx3c_basis* orb, int a, int b, int la, int lb, std::vector<int>& primA,
-                       std::vector<int>& primB, int prefer);
+                       std::vector<int>& primB);
 }  // namespace lx3c

@@ -64,18 +64,16 @@ std::map<int, unsigned char*> g_na_base;  // per device: scratch address, set up
 std::vector<double> g_na_boys, g_na_mid;
 
 // Split the primitive pairs of every pair by orientation with the planned
-// path's rule (split_orientation): a pair keeps one orientation when one has
-// its worst weighted HRR amplification at most amp_max -- the preferred
-// (cheaper) one if it qualifies, else the other; with prefer = -1 the one with
-// the smaller amplification -- otherwise each primitive pair runs on its more
-// compact centre.  Sub-pair p of list o holds
+// path's rule (split_orientation): a pair keeps one orientation, the one with
+// the smaller worst weighted HRR amplification, when that is at most amp_max;
+// otherwise each primitive pair runs on its more compact centre.  Sub-pair p of list o holds
 // its primitive indices at prim[o][p*kab ...].  A sub-pair with no primitive
 // pairs is skipped by the integral kernel; list 1 accumulates onto list 0's
 // store only where list 0 has primitive pairs for that pair.
 __global__ void noalloc_orient(const int32_t* __restrict__ pairs, long long npair, int la, int lb, int ka, int kb,
                                const int64_t* __restrict__ off, const double* __restrict__ xyz,
                                const double* __restrict__ exps, const double* __restrict__ coefs, double amp_max,
-                               int prefer, int4* __restrict__ sub, int* __restrict__ prim) {
+                               int4* __restrict__ sub, int* __restrict__ prim) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= npair) return;
   const int kab = ka * kb;
@@ -99,15 +97,8 @@ __global__ void noalloc_orient(const int32_t* __restrict__ pairs, long long npai
       worstB = fmax(worstB, pow((dab + sg) / (zb / g * dab + sg), (double)la) * f);
     }
   int whole = -1;
-  if (lb == 0) {
-    whole = 0;
-  } else if (prefer < 0) {
-    if (fmin(worstA, worstB) <= amp_max) whole = worstB < worstA ? 1 : 0;
-  } else {
-    const double wp = prefer ? worstB : worstA, wo = prefer ? worstA : worstB;
-    if (wp <= amp_max) whole = prefer;
-    else if (wo <= amp_max) whole = 1 - prefer;
-  }
+  if (lb == 0) whole = 0;
+  else if (fmin(worstA, worstB) <= amp_max) whole = worstB < worstA ? 1 : 0;
   int na = 0, nb = 0;
   for (int ia = 0; ia < ka; ++ia)
     for (int ib = 0; ib < kb; ++ib) {
@@ -207,12 +198,10 @@ extern "C" lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb
   // call may wait for work already queued on st before it returns.
   const ClassTables* cts[2];
   const NaBlob* nb = nullptr;
-  int prefer = 0;
   try {
     cts[0] = &class_tables(la, lb, lc, bra_pure ? 1 : 0);
     cts[1] = &class_tables(lb, la, lc, bra_pure ? 1 : 0);
     nb = &na_blob(la, lb, lc, bra_pure ? 1 : 0, split);
-    prefer = cheaper_orientation(la, lb, lc, bra_pure ? 1 : 0, ka * kb, kc);
   } catch (std::exception& ex) {
     return na_fail(LX3C_ENOTSUP, ex.what());
   }
@@ -226,7 +215,7 @@ extern "C" lx3c_status lx3c_eri3c_noalloc(int la, int lb, int lc, int ka, int kb
   if (e == cudaSuccess) e = launch_aux_precompute(aux, auxs, naux, kc, auxrec, auxc, st);
   if (e == cudaSuccess) {
     noalloc_orient<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pairs, npair, la, lb, ka, kb, orb_off, orb_xyz,
-                                                                     orb_exps, orb_coefs, orientation_amp_max(), prefer, sub, prim);
+                                                                     orb_exps, orb_coefs, orientation_amp_max(), sub, prim);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return na_fail(LX3C_ECUDA, cudaGetErrorString(e));

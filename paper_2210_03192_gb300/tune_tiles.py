@@ -15,8 +15,8 @@ classes alike) when its best candidate beats the default by more than
 
 Classes: every (la, lb | lc) with (K_a, K_b) pairs of the DF-J and batch
 orbital recipes (s K=6, p K=3, d/f/g K=1) and of the sweep (K_a = K_b in
-{3, 6}), la + lb <= --lmax-ab (default 3), kab >= 3, heaviest contraction
-first; tuning stops after --budget seconds.
+{3, 6}), --lmin-ab <= la + lb <= --lmax-ab (default 0..3), kab >= 3,
+heaviest contraction first; tuning stops after --budget seconds.
 
     python -m paper_2210_03192_gb300.tune_tiles [--out FILE] [--npair N] [--budget S] [--append]
 """
@@ -27,12 +27,12 @@ TS = (1, 2, 4, 8, 16, 32, 64, 128, 256)
 GS = (1, 2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 32, 36)
 
 
-def class_list(lmax_ab=3):
+def class_list(lmax_ab=3, lmin_ab=0):
     ks = {0: 6, 1: 3, 2: 1, 3: 1, 4: 1}
     out = set()
     for la in range(5):
         for lb in range(5):
-            if la + lb > lmax_ab:
+            if la + lb > lmax_ab or la + lb < lmin_ab:
                 continue
             pairs = {(ks[la], ks[lb])}
             pairs |= {(3, 3), (6, 6)}
@@ -51,6 +51,7 @@ def main(argv=None):
     ap.add_argument("--npair", type=int, default=256)
     ap.add_argument("--budget", type=float, default=600.0, help="stop after this many seconds")
     ap.add_argument("--lmax-ab", type=int, default=3)
+    ap.add_argument("--lmin-ab", type=int, default=0)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--margin", type=float, default=0.03)
     ap.add_argument("--classes", nargs="*", default=None, help="subset la,lb,lc,Ka,Kb")
@@ -59,7 +60,7 @@ def main(argv=None):
     import paper_2210_03192_gb300 as lx
     from paper_2210_03192_gb300 import workloads as W
 
-    classes = class_list(args.lmax_ab)
+    classes = class_list(args.lmax_ab, args.lmin_ab)
     if args.classes:
         classes = [tuple(int(x) for x in c.split(",")) for c in args.classes]
 
@@ -74,7 +75,8 @@ def main(argv=None):
             e.record()
             torch.cuda.synchronize()
             best = min(best, s.elapsed_time(e))
-        shape = (plan.shapes[0]["T"], plan.shapes[0]["G"])
+        used = [sh for sh in plan.shapes if sh["nsub"] > 0]
+        shape = (used[0]["T"], used[0]["G"]) if used else (0, 0)
         del plan, out
         return best, shape
 
