@@ -197,28 +197,46 @@ def test_tile_hints_fix_the_tile_and_take_precedence(tmp_path):
         lx.shape_hint(0, 0, 5, 36, 1, 0)
 
 def test_committed_shape_hints_file():
-    """The shipped GB300 hints: every line a valid class with a 1-3 CTA target,
-    loadable, and each hinted shape fits the shared memory of its target."""
+    """The shipped GB300 hints: every line a valid class with a 1-3 CTA target
+    or a (T, G) tile, loadable; a tile hint decides its class's shape (G
+    balanced over the chunks) and fits one CTA's shared memory; a CTA hint
+    decides the others' and fits its target's."""
     import paper_2210_03192_gb300 as lx
-    lines = []
+    ctas_lines, tile_lines = [], []
     with open(lx.HINTS_GB300) as f:
         for line in f:
             fields = line.split("#", 1)[0].split()
-            if fields:
-                lines.append(tuple(int(x) for x in fields))
-    assert lines
-    for (la, lb, lc, pure, kab, kc, ctas) in lines:
+            if not fields:
+                continue
+            v = tuple(int(x) for x in fields)
+            assert len(v) in (7, 9), v
+            (tile_lines if len(v) == 9 else ctas_lines).append(v)
+    assert ctas_lines and tile_lines
+    for (la, lb, lc, pure, kab, kc, ctas) in ctas_lines:
         assert 0 <= la <= 4 and 0 <= lb <= 4 and 0 <= lc <= 6 and pure == 1 and kab in (1, 9, 36) and kc == 1
         assert ctas in (1, 3)
+    for (la, lb, lc, pure, kab, kc, zero, T, G) in tile_lines:
+        assert 0 <= la <= 4 and 0 <= lb <= 4 and 0 <= lc <= 6 and pure == 1 and kc == 1 and zero == 0
+        assert kab in (3, 6, 9, 18, 36) and 1 <= T <= 512 and 1 <= G <= kab
+    tiled = {v[:6]: v for v in tile_lines}
     try:
-        assert lx.load_shape_hints() == len(lines)
-        for (la, lb, lc, pure, kab, kc, ctas) in lines:
+        assert lx.load_shape_hints() == len(ctas_lines) + len(tile_lines)
+        for (la, lb, lc, pure, kab, kc, zero, T, G) in tiled.values():
+            nch = -(-kab * kc // G)
+            Tq, Gq, mode, sb = lx.shape_query(la, lb, lc, kab, kc, 512, 0)
+            assert (Tq, Gq) == (T, -(-kab * kc // nch)) and mode == (0 if T >= 32 else 1)
+            assert sb <= 233472 - 1024
+        for (la, lb, lc, pure, kab, kc, ctas) in ctas_lines:
+            if (la, lb, lc, pure, kab, kc) in tiled:
+                continue
             T, G, mode, sb = lx.shape_query(la, lb, lc, kab, kc, 512, 0)
             assert (T, G, mode, sb) == lx.shape_query(la, lb, lc, kab, kc, 512, ctas)
             assert sb <= 233472 // ctas - 1024 or ctas == 1
     finally:
-        for (la, lb, lc, pure, kab, kc, ctas) in lines:
+        for (la, lb, lc, pure, kab, kc, ctas) in ctas_lines:
             lx.shape_hint(la, lb, lc, kab, kc, 0)
+        for v in tile_lines:
+            lx.tile_hint(v[0], v[1], v[2], v[4], v[5], 0, 0)
 
 
 def test_more_entry_points_reject_bad_arguments_on_host():
