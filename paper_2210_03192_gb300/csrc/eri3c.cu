@@ -1006,6 +1006,110 @@ __global__ void __launch_bounds__(kThreads, 3) eri3c_contract_kernel(const __gri
   for (long long tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) tile_body<2>(d, tile, sm);
 }
 
+// (s s|C) classes (la = lb = 0) stored per integral, one thread per triple.
+// With a = 0 the n-quantum CVRR2 has the single term u = 0, so the (0 0|c)
+// target is the prerequisite P_c = sum over primitive triples of
+// [00|0]^(lc) X^c (Eq. a0cv2, k = 0; X = (gamma / (gamma + zeta_c)) PC), the
+// same quantities the tile kernel forms.  The NC accumulators live in
+// registers and the primitive loop has no barrier; the ket transform runs
+// from a shared-memory copy, and the block stores its triples' blocks
+// element-major (coalesced when the triples' blocks are contiguous).
+constexpr int kSsThreads = 128;
+
+template <int LC>
+__global__ void __launch_bounds__(kSsThreads) eri3c_ss_kernel(const __grid_constant__ ClassDesc d) {
+  constexpr int NC = (LC + 1) * (LC + 2) / 2, NS = 2 * LC + 1;
+  __shared__ double sP[kSsThreads * (NC + 1)];
+  __shared__ double sO[kSsThreads * NS];
+  __shared__ long long sOff[kSsThreads];
+  __shared__ int sAcc[kSsThreads];
+  const int tid = threadIdx.x;
+  const long long ntri = d.nsub * d.naux;
+  for (long long base = (long long)blockIdx.x * kSsThreads; base < ntri; base += (long long)gridDim.x * kSsThreads) {
+    const long long w = base + tid;
+    const bool live = w < ntri;
+    double acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    long long off = -1;
+    int accum = 0;
+    if (live) {
+      const long long sub = w / d.naux;
+      const long long q = w - sub * d.naux;
+      const int4 sp = __ldg(d.subpairs + sub);
+      const long long pair = sp.x;
+      accum = sp.w;
+      off = ((pair - d.out_pair0) * d.naux + q) * (long long)d.nblk;
+      const double Cx = __ldg(d.auxc + 3 * q), Cy = __ldg(d.auxc + 3 * q + 1), Cz = __ldg(d.auxc + 3 * q + 2);
+      for (int ip = 0; ip < sp.z; ++ip) {
+        const double* pr = d.pairrec + (pair * d.Kab_rec + __ldg(d.primidx + sp.y + ip)) * kPairRec;
+        const double gam = __ldg(pr + PR_G), K = __ldg(pr + PR_K);
+        const double PCx = __ldg(pr + PR_P) - Cx, PCy = __ldg(pr + PR_P + 1) - Cy, PCz = __ldg(pr + PR_P + 2) - Cz;
+        const double pc2 = fma(PCz, PCz, fma(PCy, PCy, PCx * PCx));
+        for (int ic = 0; ic < d.Kc; ++ic) {
+          const double zc = __ldg(d.auxrec + (q * d.Kc + ic) * kAuxRec);
+          const double ccp = __ldg(d.auxrec + (q * d.Kc + ic) * kAuxRec + 1);
+          const double sg = gam + zc;
+          const double rs = rsqrt_fp64(sg);
+          const double r = rs * rs;
+          const double gr = gam * r;
+          const double Tb = gam * zc * r * pc2;
+          double V;
+          boys_scaled(d.boys_tab, d.boys_mid, d.boys_cL, LC, LC, Tb, K * ccp * rs, &V, 0);
+          if (LC == 0) {
+            acc[0] += V;
+          } else {
+            // powers of X = gr PC, the monomials X^c in the Cartesian order
+            // (x descending, then y descending), one FMA per target
+            double px[LC + 1], py[LC + 1], pz[LC + 1];
+            px[0] = V; py[0] = 1.0; pz[0] = 1.0;
+            const double Xx = gr * PCx, Xy = gr * PCy, Xz = gr * PCz;
+#pragma unroll
+            for (int j = 1; j <= LC; ++j) {
+              px[j] = px[j - 1] * Xx;
+              py[j] = py[j - 1] * Xy;
+              pz[j] = pz[j - 1] * Xz;
+            }
+            int c = 0;
+#pragma unroll
+            for (int nx = LC; nx >= 0; --nx)
+#pragma unroll
+              for (int ny = LC - nx; ny >= 0; --ny) {
+                acc[c] = fma(px[nx], py[ny] * pz[LC - nx - ny], acc[c]);
+                ++c;
+              }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sP[tid * (NC + 1) + c] = acc[c];
+    sOff[tid] = off;
+    sAcc[tid] = accum;
+    __syncthreads();
+    // ket transform: element-major over the block's triples
+    for (int i = tid; i < kSsThreads * NS; i += kSsThreads) {
+      const int t = i / NS, C = i - t * NS;
+      double v = 0.0;
+      for (int k = __ldg(d.kptr + C); k < __ldg(d.kptr + C + 1); ++k) {
+        const int2 e = __ldg(d.kent + k);
+        v = fma(__ldg(d.pal + e.y), sP[t * (NC + 1) + e.x], v);
+      }
+      sO[i] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < kSsThreads * NS; i += kSsThreads) {
+      const int t = i / NS, C = i - t * NS;
+      const long long o = sOff[t];
+      if (o < 0) continue;
+      double v = sO[i];
+      if (sAcc[t]) v += d.out[o + C];
+      d.out[o + C] = v;
+    }
+    __syncthreads();
+  }
+}
+
 // The bra map M of every sub-pair of a launch (digest 5): HRR and bra
 // transforms applied to the unit vectors, i.e. the class stages with the nkrow
 // rows of the identity in place of (e 0|C) (the descriptor has nC = nkrow,
@@ -1163,7 +1267,20 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (d.digest == 5)
+  if (d.digest == 0 && d.la == 0 && d.lb == 0 && d.orient == 0) {
+    // (s s|C): the register-resident form, one thread per triple
+    const long long nb = (d.nsub * d.naux + kSsThreads - 1) / kSsThreads;
+    const unsigned g = (unsigned)std::min<long long>(std::max<long long>(nb, 1), 152LL * 32);
+    switch (d.lc) {
+      case 0: eri3c_ss_kernel<0><<<g, kSsThreads, 0, st>>>(d); break;
+      case 1: eri3c_ss_kernel<1><<<g, kSsThreads, 0, st>>>(d); break;
+      case 2: eri3c_ss_kernel<2><<<g, kSsThreads, 0, st>>>(d); break;
+      case 3: eri3c_ss_kernel<3><<<g, kSsThreads, 0, st>>>(d); break;
+      case 4: eri3c_ss_kernel<4><<<g, kSsThreads, 0, st>>>(d); break;
+      case 5: eri3c_ss_kernel<5><<<g, kSsThreads, 0, st>>>(d); break;
+      default: eri3c_ss_kernel<6><<<g, kSsThreads, 0, st>>>(d); break;
+    }
+  } else if (d.digest == 5)
     eri3c_contract_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);
   else if (d.digest == 4)
     eri3c_multi_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);

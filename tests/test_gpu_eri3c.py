@@ -55,10 +55,19 @@ def test_cartesian_bra(lx, la, lb, lc):
 
 
 @pytest.mark.parametrize("la,lb,lc,Ka,Kb,Kc", [(2, 2, 2, 6, 6, 1), (1, 0, 3, 3, 2, 3), (4, 4, 6, 6, 6, 1),
-                                                (0, 0, 0, 6, 6, 4), (3, 1, 4, 1, 6, 2)])
+                                                (0, 0, 0, 6, 6, 4), (3, 1, 4, 1, 6, 2), (0, 0, 5, 3, 6, 2)])
 def test_high_contraction(lx, la, lb, lc, Ka, Kb, Kc):
     p = W.class_problem(la, lb, lc, 3, 40, Ka, Kb, Kc, box=8.0, exp_lo=0.05, exp_hi=1e4,
                         seed=300 + la + 10 * lb + 100 * lc)
+    assert_parity(run(lx, p), p)
+
+
+@pytest.mark.parametrize("lc", [0, 4, 6])
+def test_ss_classes_across_blocks(lx, lc):
+    """(s s|C) runs one thread per triple in 128-triple blocks: 70 pairs x 37
+    kets (2,590 triples, 21 blocks, the last one ragged), contracted on both
+    sides of the bra and in the ket, every integral against the oracle."""
+    p = W.class_problem(0, 0, lc, 70, 37, 3, 2, 2, box=8.0, exp_lo=0.05, exp_hi=1e4, seed=4200 + lc)
     assert_parity(run(lx, p), p)
 
 
