@@ -1016,6 +1016,54 @@ __global__ void __launch_bounds__(kThreads, 3) eri3c_contract_kernel(const __gri
 // element-major (coalesced when the triples' blocks are contiguous).
 constexpr int kSsThreads = 128;
 
+// The primitive loop of one (s s|C) triple: acc[c] += [00|0]^(lc) X^c over
+// the sub-pair's primitive pairs and the ket shell's primitives.
+template <int LC>
+__device__ __forceinline__ void ss_prims(const ClassDesc& d, long long pair, const int4& sp, long long q,
+                                         double* acc) {
+  const double Cx = __ldg(d.auxc + 3 * q), Cy = __ldg(d.auxc + 3 * q + 1), Cz = __ldg(d.auxc + 3 * q + 2);
+  for (int ip = 0; ip < sp.z; ++ip) {
+    const double* pr = d.pairrec + (pair * d.Kab_rec + __ldg(d.primidx + sp.y + ip)) * kPairRec;
+    const double gam = __ldg(pr + PR_G), K = __ldg(pr + PR_K);
+    const double PCx = __ldg(pr + PR_P) - Cx, PCy = __ldg(pr + PR_P + 1) - Cy, PCz = __ldg(pr + PR_P + 2) - Cz;
+    const double pc2 = fma(PCz, PCz, fma(PCy, PCy, PCx * PCx));
+    for (int ic = 0; ic < d.Kc; ++ic) {
+      const double zc = __ldg(d.auxrec + (q * d.Kc + ic) * kAuxRec);
+      const double ccp = __ldg(d.auxrec + (q * d.Kc + ic) * kAuxRec + 1);
+      const double sg = gam + zc;
+      const double rs = rsqrt_fp64(sg);
+      const double r = rs * rs;
+      const double gr = gam * r;
+      const double Tb = gam * zc * r * pc2;
+      double V;
+      boys_scaled(d.boys_tab, d.boys_mid, d.boys_cL, LC, LC, Tb, K * ccp * rs, &V, 0);
+      if (LC == 0) {
+        acc[0] += V;
+      } else {
+        // powers of X = gr PC; the monomials X^c in the Cartesian order (x
+        // descending, then y descending), one FMA per target
+        double px[LC + 1], py[LC + 1], pz[LC + 1];
+        px[0] = V; py[0] = 1.0; pz[0] = 1.0;
+        const double Xx = gr * PCx, Xy = gr * PCy, Xz = gr * PCz;
+#pragma unroll
+        for (int j = 1; j <= LC; ++j) {
+          px[j] = px[j - 1] * Xx;
+          py[j] = py[j - 1] * Xy;
+          pz[j] = pz[j - 1] * Xz;
+        }
+        int c = 0;
+#pragma unroll
+        for (int nx = LC; nx >= 0; --nx)
+#pragma unroll
+          for (int ny = LC - nx; ny >= 0; --ny) {
+            acc[c] = fma(px[nx], py[ny] * pz[LC - nx - ny], acc[c]);
+            ++c;
+          }
+      }
+    }
+  }
+}
+
 template <int LC>
 __global__ void __launch_bounds__(kSsThreads) eri3c_ss_kernel(const __grid_constant__ ClassDesc d) {
   constexpr int NC = (LC + 1) * (LC + 2) / 2, NS = 2 * LC + 1;
@@ -1027,60 +1075,18 @@ __global__ void __launch_bounds__(kSsThreads) eri3c_ss_kernel(const __grid_const
   const long long ntri = d.nsub * d.naux;
   for (long long base = (long long)blockIdx.x * kSsThreads; base < ntri; base += (long long)gridDim.x * kSsThreads) {
     const long long w = base + tid;
-    const bool live = w < ntri;
     double acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = 0.0;
     long long off = -1;
     int accum = 0;
-    if (live) {
+    if (w < ntri) {
       const long long sub = w / d.naux;
       const long long q = w - sub * d.naux;
       const int4 sp = __ldg(d.subpairs + sub);
-      const long long pair = sp.x;
       accum = sp.w;
-      off = ((pair - d.out_pair0) * d.naux + q) * (long long)d.nblk;
-      const double Cx = __ldg(d.auxc + 3 * q), Cy = __ldg(d.auxc + 3 * q + 1), Cz = __ldg(d.auxc + 3 * q + 2);
-      for (int ip = 0; ip < sp.z; ++ip) {
-        const double* pr = d.pairrec + (pair * d.Kab_rec + __ldg(d.primidx + sp.y + ip)) * kPairRec;
-        const double gam = __ldg(pr + PR_G), K = __ldg(pr + PR_K);
-        const double PCx = __ldg(pr + PR_P) - Cx, PCy = __ldg(pr + PR_P + 1) - Cy, PCz = __ldg(pr + PR_P + 2) - Cz;
-        const double pc2 = fma(PCz, PCz, fma(PCy, PCy, PCx * PCx));
-        for (int ic = 0; ic < d.Kc; ++ic) {
-          const double zc = __ldg(d.auxrec + (q * d.Kc + ic) * kAuxRec);
-          const double ccp = __ldg(d.auxrec + (q * d.Kc + ic) * kAuxRec + 1);
-          const double sg = gam + zc;
-          const double rs = rsqrt_fp64(sg);
-          const double r = rs * rs;
-          const double gr = gam * r;
-          const double Tb = gam * zc * r * pc2;
-          double V;
-          boys_scaled(d.boys_tab, d.boys_mid, d.boys_cL, LC, LC, Tb, K * ccp * rs, &V, 0);
-          if (LC == 0) {
-            acc[0] += V;
-          } else {
-            // powers of X = gr PC, the monomials X^c in the Cartesian order
-            // (x descending, then y descending), one FMA per target
-            double px[LC + 1], py[LC + 1], pz[LC + 1];
-            px[0] = V; py[0] = 1.0; pz[0] = 1.0;
-            const double Xx = gr * PCx, Xy = gr * PCy, Xz = gr * PCz;
-#pragma unroll
-            for (int j = 1; j <= LC; ++j) {
-              px[j] = px[j - 1] * Xx;
-              py[j] = py[j - 1] * Xy;
-              pz[j] = pz[j - 1] * Xz;
-            }
-            int c = 0;
-#pragma unroll
-            for (int nx = LC; nx >= 0; --nx)
-#pragma unroll
-              for (int ny = LC - nx; ny >= 0; --ny) {
-                acc[c] = fma(px[nx], py[ny] * pz[LC - nx - ny], acc[c]);
-                ++c;
-              }
-          }
-        }
-      }
+      off = (((long long)sp.x - d.out_pair0) * d.naux + q) * (long long)d.nblk;
+      ss_prims<LC>(d, sp.x, sp, q, acc);
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) sP[tid * (NC + 1) + c] = acc[c];
@@ -1107,6 +1113,59 @@ __global__ void __launch_bounds__(kSsThreads) eri3c_ss_kernel(const __grid_const
       d.out[o + C] = v;
     }
     __syncthreads();
+  }
+}
+
+// (s s|C) DF-J launches digesting per integral (digest == 1), one warp per
+// tile, lanes over the tile's kets: gamma_P[C] += w D_ab (ss|P)_C per lane,
+// and J_ab += w_J sum over the tile's kets and C of (ss|P)_C c_PC, reduced
+// across the warp into one add.  The same sums as the tile kernel's digest.
+template <int LC>
+__global__ void __launch_bounds__(kSsThreads) eri3c_ss_dfj_kernel(const __grid_constant__ ClassDesc d) {
+  constexpr int NC = (LC + 1) * (LC + 2) / 2, NS = 2 * LC + 1;
+  __shared__ double sP[kSsThreads * (NC + 1)];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* row = sP + threadIdx.x * (NC + 1);
+  const long long nwarps = (long long)gridDim.x * (kSsThreads / 32);
+  for (long long tile = blockIdx.x * (long long)(kSsThreads / 32) + warp; tile < d.ntiles; tile += nwarps) {
+    const int4 tt = __ldg(d.tiles + tile);
+    const int4 sp = __ldg(d.subpairs + tt.x);
+    const long long pair = sp.x;
+    const int4 pao = __ldg(d.pair_ao + pair);
+    const double wg = pao.z ? 1.0 : 2.0, wj = pao.z ? 0.5 : 1.0;
+    const double Dab = d.gacc ? __ldg(d.D + (long long)pao.x * d.ldD + pao.y) : 0.0;
+    double jsum = 0.0;
+    for (int t0 = 0; t0 < tt.z; t0 += 32) {
+      const int t = t0 + lane;
+      const bool live = t < tt.z;
+      double acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+      const long long q = tt.y + t;
+      if (live) ss_prims<LC>(d, pair, sp, q, acc);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) row[c] = acc[c];
+      __syncwarp();
+      if (live) {
+        const int ao = __ldg(d.aux_ao + q);
+#pragma unroll
+        for (int C = 0; C < NS; ++C) {
+          double v = 0.0;
+          for (int k = __ldg(d.kptr + C); k < __ldg(d.kptr + C + 1); ++k) {
+            const int2 e = __ldg(d.kent + k);
+            v = fma(__ldg(d.pal + e.y), row[e.x], v);
+          }
+          if (d.gacc) fix_add(d.gacc + kFixWords * (ao + C), wg * Dab * v);
+          if (d.Jacc) jsum = fma(v, __ldg(d.cvec + ao + C), jsum);
+        }
+      }
+      __syncwarp();
+    }
+    if (d.Jacc) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) jsum += __shfl_xor_sync(0xffffffffu, jsum, o);
+      if (lane == 0) fix_add(d.Jacc + kFixWords * ((long long)pao.x * d.ldD + pao.y), wj * jsum);
+    }
   }
 }
 
@@ -1279,6 +1338,19 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
       case 4: eri3c_ss_kernel<4><<<g, kSsThreads, 0, st>>>(d); break;
       case 5: eri3c_ss_kernel<5><<<g, kSsThreads, 0, st>>>(d); break;
       default: eri3c_ss_kernel<6><<<g, kSsThreads, 0, st>>>(d); break;
+    }
+  } else if (d.digest == 1 && d.la == 0 && d.lb == 0 && d.orient == 0 && d.tiles) {
+    // (s s|C) DF-J: one warp per tile
+    const long long nb = (d.ntiles + kSsThreads / 32 - 1) / (kSsThreads / 32);
+    const unsigned g = (unsigned)std::min<long long>(std::max<long long>(nb, 1), 152LL * 32);
+    switch (d.lc) {
+      case 0: eri3c_ss_dfj_kernel<0><<<g, kSsThreads, 0, st>>>(d); break;
+      case 1: eri3c_ss_dfj_kernel<1><<<g, kSsThreads, 0, st>>>(d); break;
+      case 2: eri3c_ss_dfj_kernel<2><<<g, kSsThreads, 0, st>>>(d); break;
+      case 3: eri3c_ss_dfj_kernel<3><<<g, kSsThreads, 0, st>>>(d); break;
+      case 4: eri3c_ss_dfj_kernel<4><<<g, kSsThreads, 0, st>>>(d); break;
+      case 5: eri3c_ss_dfj_kernel<5><<<g, kSsThreads, 0, st>>>(d); break;
+      default: eri3c_ss_dfj_kernel<6><<<g, kSsThreads, 0, st>>>(d); break;
     }
   } else if (d.digest == 5)
     eri3c_contract_kernel<<<grid, kThreads, (size_t)d.smem_doubles * 8, st>>>(d);

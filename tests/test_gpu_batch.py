@@ -53,10 +53,14 @@ def test_batch_graph_equals_plain_and_oracle(lx):
     g0, J0 = b.execute(mode=0)
     torch.cuda.synchronize()
     for m, cl in enumerate(mols):
-        # same tiles and exact fixed-point sums: the three modes agree bit for bit
-        for g, J in ((g1[m], J1[m]), (g2[m], J2[m])):
-            assert np.array_equal(g, g0[m].cpu().numpy())
-            assert np.array_equal(J, J0[m].cpu().numpy())
+        # the class launches on graph branches and the per-class launches run
+        # the same kernels into exact fixed-point sums: bit for bit equal; the
+        # persistent kernels run the tile body for every class, (s s|C)
+        # included, whose products round in another order: equal to rounding
+        g0m, J0m = g0[m].cpu().numpy(), J0[m].cpu().numpy()
+        assert np.array_equal(g2[m], g0m) and np.array_equal(J2[m], J0m)
+        assert np.abs(g1[m] - g0m).max() <= 1e-12 * np.abs(g0m).max()
+        assert np.abs(J1[m] - J0m).max() <= 1e-12 * np.abs(J0m).max()
     assert info["branch_kernels"] == info["graph_kernels"] - info["tiers"] + info["class_launches"]
     # oracle on the smallest molecule, same screened tasks
     cl = mols[0]
@@ -101,10 +105,11 @@ def test_batch_members_of_the_16_molecule_workload(lx):
         g, J = b.execute(mode)
         torch.cuda.synchronize()
         res[mode] = ([x.cpu().numpy().copy() for x in g], [x.cpu().numpy().copy() for x in J])
-    for mode in (1, 2):
-        for m in range(2):
-            assert np.array_equal(res[mode][0][m], res[0][0][m])
-            assert np.array_equal(res[mode][1][m], res[0][1][m])
+    for m in range(2):
+        assert np.array_equal(res[2][0][m], res[0][0][m]) and np.array_equal(res[2][1][m], res[0][1][m])
+        for k in (0, 1):  # the persistent kernels: equal to rounding (see above)
+            ref = res[0][k][m]
+            assert np.abs(res[1][k][m] - ref).max() <= 1e-12 * np.abs(ref).max()
     cl = mols[0]
     plan = lx.DFJPlan(cl.orb, cl.aux, 1e-12)  # the same screen, for its task list
     g, J = res[2][0][0], res[2][1][0]
