@@ -301,9 +301,9 @@ lx3c_status lx3c_cvrr2_expansion(const int32_t* a, const int32_t* c, int32_t cap
  * lx3c_dfj_execute: D (device, nao x nao row-major, symmetric), c (device,
  *   naux_ao) in; gamma (device, naux_ao) and J (device, nao x nao, symmetric)
  *   overwritten; either output may be NULL to skip it (not both).
- *   Asynchronous on `stream`.  gamma and J are summed exactly in 128-bit
- *   fixed point (each contribution rounded to a multiple of 2^-72, every
- *   partial sum below 2^55 in magnitude) and rounded once to FP64, so the
+ *   Asynchronous on `stream`.  gamma and J are summed exactly in fixed point
+ *   (each contribution rounded to a multiple of 2^-72, every partial sum
+ *   below 2^55 in magnitude) and rounded once to FP64, so the
  *   result does not depend on the order in which tiles finish: repeated
  *   executes of a plan are bitwise equal.
  * lx3c_dfj_execute_multi: the same build for nd (1..8) densities and
@@ -462,7 +462,10 @@ lx3c_status lx3c_dfj_coulomb(lx3c_dfj* plan, const double* L, int64_t lda, const
  * lx3c_batch_execute: mode 1 or 2 launches graph 1 or 2 (one
  *   cudaGraphLaunch on `stream`); mode 0 runs the same tasks as per-class
  *   launches (lx3c_dfj_execute per molecule), for comparison; any other mode
- *   is LX3C_EINVAL.  Asynchronous.
+ *   is LX3C_EINVAL.  Asynchronous.  Modes 0 and 2 run the same kernels and
+ *   give bitwise equal results; mode 1's persistent kernels run the tile form
+ *   for every class ((s s|C) included, which the class launches run
+ *   register-resident), so mode 1 agrees with them to rounding.
  * lx3c_batch_info: out[0..15] = molecules, screened triples, integrals,
  *   algorithmic flops, plain kernel launches, persistent-graph kernel nodes,
  *   work items, class launches merged, persistent smem bytes, persistent

@@ -1169,6 +1169,255 @@ __global__ void __launch_bounds__(kSsThreads) eri3c_ss_dfj_kernel(const __grid_c
   }
 }
 
+// (p s|C) classes, lc <= 4: la = 1, lb = 0 in the A orientation, or the
+// (s p|C) class run B-oriented (recurrences on the p shell, no HRR).  With
+// a = 1_i the n-quantum CVRR2 has two terms,
+//   (1_i 0|c) = (1_i 0)_{0,c} + c_i (0 0)_{1,c-1_i}    (Eq. cVRR2),
+// whose prerequisites are A_i(c) = sum [1_i 0|0]^(lc) X^c and
+// B(n) = sum [00|0]^(lc) Y X^n (Eq. a0cv2, Y = 1/(2(gamma+zeta_c))), with
+// [1_i 0|0]^(lc) = PA_i [00|0]^(lc) - (rho/gamma) PC_i [00|0]^(lc+1)
+// (Eq. vrr1): 3 ncart(lc) + ncart(lc-1) accumulators held in registers.
+constexpr int kPsThreads = 64;
+
+template <int LC>
+__device__ __forceinline__ void ps_prims(const ClassDesc& d, long long pair, const int4& sp, long long q,
+                                         double (&A)[3][(LC + 1) * (LC + 2) / 2], double* Bm) {
+  const double Cx = __ldg(d.auxc + 3 * q), Cy = __ldg(d.auxc + 3 * q + 1), Cz = __ldg(d.auxc + 3 * q + 2);
+  const int fpa = d.orient ? PR_PB : PR_PA;
+  for (int ip = 0; ip < sp.z; ++ip) {
+    const double* pr = d.pairrec + (pair * d.Kab_rec + __ldg(d.primidx + sp.y + ip)) * kPairRec;
+    const double gam = __ldg(pr + PR_G), K = __ldg(pr + PR_K);
+    const double PAx = __ldg(pr + fpa), PAy = __ldg(pr + fpa + 1), PAz = __ldg(pr + fpa + 2);
+    const double PCx = __ldg(pr + PR_P) - Cx, PCy = __ldg(pr + PR_P + 1) - Cy, PCz = __ldg(pr + PR_P + 2) - Cz;
+    const double pc2 = fma(PCz, PCz, fma(PCy, PCy, PCx * PCx));
+    for (int ic = 0; ic < d.Kc; ++ic) {
+      const double zc = __ldg(d.auxrec + (q * d.Kc + ic) * kAuxRec);
+      const double ccp = __ldg(d.auxrec + (q * d.Kc + ic) * kAuxRec + 1);
+      const double sg = gam + zc;
+      const double rs = rsqrt_fp64(sg);
+      const double r = rs * rs;
+      const double gr = gam * r, rg = zc * r;
+      const double Tb = gam * zc * r * pc2;
+      double v2[2];
+      boys_scaled(d.boys_tab, d.boys_mid, d.boys_cL, LC + 1, LC, Tb, K * ccp * rs, v2, 1);
+      const double V0 = v2[0];
+      const double Vx = fma(-rg * PCx, v2[1], PAx * V0), Vy = fma(-rg * PCy, v2[1], PAy * V0),
+                   Vz = fma(-rg * PCz, v2[1], PAz * V0);
+      double px[LC + 1], py[LC + 1], pz[LC + 1];
+      px[0] = 1.0; py[0] = 1.0; pz[0] = 1.0;
+      const double Xx = gr * PCx, Xy = gr * PCy, Xz = gr * PCz;
+#pragma unroll
+      for (int j = 1; j <= LC; ++j) {
+        px[j] = px[j - 1] * Xx;
+        py[j] = py[j - 1] * Xy;
+        pz[j] = pz[j - 1] * Xz;
+      }
+      int c = 0;
+#pragma unroll
+      for (int nx = LC; nx >= 0; --nx)
+#pragma unroll
+        for (int ny = LC - nx; ny >= 0; --ny) {
+          const double m = px[nx] * (py[ny] * pz[LC - nx - ny]);
+          A[0][c] = fma(Vx, m, A[0][c]);
+          A[1][c] = fma(Vy, m, A[1][c]);
+          A[2][c] = fma(Vz, m, A[2][c]);
+          ++c;
+        }
+      if (LC > 0) {
+        const double VY = V0 * (0.5 * r);
+        int n = 0;
+#pragma unroll
+        for (int nx = LC - 1; nx >= 0; --nx)
+#pragma unroll
+          for (int ny = LC - 1 - nx; ny >= 0; --ny) {
+            Bm[n] = fma(VY, px[nx] * (py[ny] * pz[LC - 1 - nx - ny]), Bm[n]);
+            ++n;
+          }
+      }
+    }
+  }
+}
+
+// The (p s|c) targets G(i, c) = A_i(c) + c_i B(c - 1_i) into row[i * (NC+1) + c].
+template <int LC>
+__device__ __forceinline__ void ps_targets(const double (&A)[3][(LC + 1) * (LC + 2) / 2], const double* Bm,
+                                           double* row) {
+  constexpr int NC = (LC + 1) * (LC + 2) / 2;
+  int c = 0;
+#pragma unroll
+  for (int nx = LC; nx >= 0; --nx)
+#pragma unroll
+    for (int ny = LC - nx; ny >= 0; --ny) {
+      const int nz = LC - nx - ny;
+      // index of c - 1_i in the Cartesian order of degree LC-1
+      double gx = A[0][c], gy = A[1][c], gz = A[2][c];
+      if (LC > 0) {
+        // position of (x, y, z) of degree LC-1: (LC-1-x)(LC-x)/2 + (LC-1-x-y)
+        if (nx > 0) gx = fma((double)nx, Bm[(LC - nx) * (LC - nx + 1) / 2 + (LC - nx - ny)], gx);
+        if (ny > 0) gy = fma((double)ny, Bm[(LC - 1 - nx) * (LC - nx) / 2 + (LC - nx - ny)], gy);
+        if (nz > 0) gz = fma((double)nz, Bm[(LC - 1 - nx) * (LC - nx) / 2 + (LC - 1 - nx - ny)], gz);
+      }
+      row[c] = gx;
+      row[(NC + 1) + c] = gy;
+      row[2 * (NC + 1) + c] = gz;
+      ++c;
+    }
+}
+
+// Ket then bra transform of one triple's targets (row: 3 x (NC+1)) into
+// out[s * NS + C], s the bra component in storage order.
+template <int LC>
+__device__ __forceinline__ void ps_transform(const ClassDesc& d, const double* row, double* out) {
+  constexpr int NC = (LC + 1) * (LC + 2) / 2, NS = 2 * LC + 1;
+  double H[3][NS];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int C = 0; C < NS; ++C) {
+      double v = 0.0;
+      for (int k = __ldg(d.kptr + C); k < __ldg(d.kptr + C + 1); ++k) {
+        const int2 e = __ldg(d.kent + k);
+        v = fma(__ldg(d.pal + e.y), row[a * (NC + 1) + e.x], v);
+      }
+      H[a][C] = v;
+    }
+  if (d.nbA) {
+#pragma unroll
+    for (int A = 0; A < 3; ++A) {
+      const int q0 = __ldg(d.baptr + A), q1 = __ldg(d.baptr + A + 1);
+#pragma unroll
+      for (int C = 0; C < NS; ++C) {
+        double v = 0.0;
+        for (int k = q0; k < q1; ++k) {
+          const int2 e = __ldg(d.baent + k);
+          // a single 3-way select keeps H in registers
+          const double h = e.x == 0 ? H[0][C] : (e.x == 1 ? H[1][C] : H[2][C]);
+          v = fma(__ldg(d.pal + e.y), h, v);
+        }
+        out[A * NS + C] = v;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int C = 0; C < NS; ++C) out[a * NS + C] = H[a][C];
+  }
+}
+
+template <int LC>
+__global__ void __launch_bounds__(kPsThreads) eri3c_ps_kernel(const __grid_constant__ ClassDesc d) {
+  constexpr int NC = (LC + 1) * (LC + 2) / 2, NS = 2 * LC + 1, NB = 3 * NS;
+  constexpr int NCM = LC > 0 ? LC * (LC + 1) / 2 : 1;
+  __shared__ double sG[kPsThreads * 3 * (NC + 1)];
+  __shared__ double sO[kPsThreads * NB];
+  __shared__ long long sOff[kPsThreads];
+  __shared__ int sAcc[kPsThreads];
+  const int tid = threadIdx.x;
+  const long long ntri = d.nsub * d.naux;
+  for (long long base = (long long)blockIdx.x * kPsThreads; base < ntri; base += (long long)gridDim.x * kPsThreads) {
+    const long long w = base + tid;
+    long long off = -1;
+    int accum = 0;
+    if (w < ntri) {
+      double A[3][NC], Bm[NCM];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) A[0][c] = A[1][c] = A[2][c] = 0.0;
+#pragma unroll
+      for (int n = 0; n < NCM; ++n) Bm[n] = 0.0;
+      const long long sub = w / d.naux;
+      const long long q = w - sub * d.naux;
+      const int4 sp = __ldg(d.subpairs + sub);
+      accum = sp.w;
+      off = (((long long)sp.x - d.out_pair0) * d.naux + q) * (long long)d.nblk;
+      ps_prims<LC>(d, sp.x, sp, q, A, Bm);
+      double* row = sG + tid * 3 * (NC + 1);
+      ps_targets<LC>(A, Bm, row);
+      ps_transform<LC>(d, row, sO + tid * NB);
+    }
+    sOff[tid] = off;
+    sAcc[tid] = accum;
+    __syncthreads();
+    for (int i = tid; i < kPsThreads * NB; i += kPsThreads) {
+      const int t = i / NB, x = i - t * NB;
+      const long long o = sOff[t];
+      if (o < 0) continue;
+      double v = sO[i];
+      if (sAcc[t]) v += d.out[o + x];
+      d.out[o + x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// (p s|C) DF-J launches digesting per integral: one warp per tile, lanes over
+// its kets; gamma_P[C] += w sum_s D_s (ps|P)_{sC} per lane and
+// J_s += w_J sum over the tile's kets and C of (ps|P)_{sC} c_PC, reduced
+// across the warp.
+template <int LC>
+__global__ void __launch_bounds__(kPsThreads) eri3c_ps_dfj_kernel(const __grid_constant__ ClassDesc d) {
+  constexpr int NC = (LC + 1) * (LC + 2) / 2, NS = 2 * LC + 1, NB = 3 * NS;
+  constexpr int NCM = LC > 0 ? LC * (LC + 1) / 2 : 1;
+  __shared__ double sG[kPsThreads * 3 * (NC + 1)];
+  __shared__ double sO[kPsThreads * NB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* row = sG + threadIdx.x * 3 * (NC + 1);
+  double* out = sO + threadIdx.x * NB;
+  const long long nwarps = (long long)gridDim.x * (kPsThreads / 32);
+  for (long long tile = blockIdx.x * (long long)(kPsThreads / 32) + warp; tile < d.ntiles; tile += nwarps) {
+    const int4 tt = __ldg(d.tiles + tile);
+    const int4 sp = __ldg(d.subpairs + tt.x);
+    const long long pair = sp.x;
+    const int4 pao = __ldg(d.pair_ao + pair);
+    const double wg = pao.z ? 1.0 : 2.0, wj = pao.z ? 0.5 : 1.0;
+    double Ds[3] = {0.0, 0.0, 0.0};
+    if (d.gacc)
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+        Ds[s] = d.orient ? __ldg(d.D + (long long)pao.x * d.ldD + pao.y + s)
+                         : __ldg(d.D + (long long)(pao.x + s) * d.ldD + pao.y);
+    double js[3] = {0.0, 0.0, 0.0};
+    for (int t0 = 0; t0 < tt.z; t0 += 32) {
+      const int t = t0 + lane;
+      if (t < tt.z) {
+        const long long q = tt.y + t;
+        double A[3][NC], Bm[NCM];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) A[0][c] = A[1][c] = A[2][c] = 0.0;
+#pragma unroll
+        for (int n = 0; n < NCM; ++n) Bm[n] = 0.0;
+        ps_prims<LC>(d, pair, sp, q, A, Bm);
+        ps_targets<LC>(A, Bm, row);
+        ps_transform<LC>(d, row, out);
+        const int ao = __ldg(d.aux_ao + q);
+#pragma unroll
+        for (int C = 0; C < NS; ++C) {
+          const double i0 = out[C], i1 = out[NS + C], i2 = out[2 * NS + C];
+          if (d.gacc) fix_add(d.gacc + kFixWords * (ao + C), wg * fma(Ds[0], i0, fma(Ds[1], i1, Ds[2] * i2)));
+          if (d.Jacc) {
+            const double cv = __ldg(d.cvec + ao + C);
+            js[0] = fma(i0, cv, js[0]);
+            js[1] = fma(i1, cv, js[1]);
+            js[2] = fma(i2, cv, js[2]);
+          }
+        }
+      }
+    }
+    if (d.Jacc) {
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        double v = js[s];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+          const long long e = d.orient ? (long long)pao.x * d.ldD + pao.y + s : (long long)(pao.x + s) * d.ldD + pao.y;
+          fix_add(d.Jacc + kFixWords * e, wj * v);
+        }
+      }
+    }
+  }
+}
+
 // The bra map M of every sub-pair of a launch (digest 5): HRR and bra
 // transforms applied to the unit vectors, i.e. the class stages with the nkrow
 // rows of the identity in place of (e 0|C) (the descriptor has nC = nkrow,
@@ -1338,6 +1587,29 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
       case 4: eri3c_ss_kernel<4><<<g, kSsThreads, 0, st>>>(d); break;
       case 5: eri3c_ss_kernel<5><<<g, kSsThreads, 0, st>>>(d); break;
       default: eri3c_ss_kernel<6><<<g, kSsThreads, 0, st>>>(d); break;
+    }
+  } else if ((d.digest == 0 || (d.digest == 1 && d.tiles)) && d.lc <= 4 &&
+             ((d.la == 1 && d.lb == 0 && d.orient == 0) || (d.la == 0 && d.lb == 1 && d.orient == 1))) {
+    // (p s|C) and B-oriented (s p|C), lc <= 4: register-resident
+    const long long items = d.digest ? d.ntiles : d.nsub * d.naux;
+    const long long per = d.digest ? kPsThreads / 32 : kPsThreads;
+    const unsigned g = (unsigned)std::min<long long>(std::max<long long>((items + per - 1) / per, 1), 152LL * 64);
+    if (d.digest) {
+      switch (d.lc) {
+        case 0: eri3c_ps_dfj_kernel<0><<<g, kPsThreads, 0, st>>>(d); break;
+        case 1: eri3c_ps_dfj_kernel<1><<<g, kPsThreads, 0, st>>>(d); break;
+        case 2: eri3c_ps_dfj_kernel<2><<<g, kPsThreads, 0, st>>>(d); break;
+        case 3: eri3c_ps_dfj_kernel<3><<<g, kPsThreads, 0, st>>>(d); break;
+        default: eri3c_ps_dfj_kernel<4><<<g, kPsThreads, 0, st>>>(d); break;
+      }
+    } else {
+      switch (d.lc) {
+        case 0: eri3c_ps_kernel<0><<<g, kPsThreads, 0, st>>>(d); break;
+        case 1: eri3c_ps_kernel<1><<<g, kPsThreads, 0, st>>>(d); break;
+        case 2: eri3c_ps_kernel<2><<<g, kPsThreads, 0, st>>>(d); break;
+        case 3: eri3c_ps_kernel<3><<<g, kPsThreads, 0, st>>>(d); break;
+        default: eri3c_ps_kernel<4><<<g, kPsThreads, 0, st>>>(d); break;
+      }
     }
   } else if (d.digest == 1 && d.la == 0 && d.lb == 0 && d.orient == 0 && d.tiles) {
     // (s s|C) DF-J: one warp per tile

@@ -62,13 +62,17 @@ def test_high_contraction(lx, la, lb, lc, Ka, Kb, Kc):
     assert_parity(run(lx, p), p)
 
 
-@pytest.mark.parametrize("lc", [0, 4, 6])
-def test_ss_classes_across_blocks(lx, lc):
-    """(s s|C) runs one thread per triple in 128-triple blocks: 70 pairs x 37
-    kets (2,590 triples, 21 blocks, the last one ragged), contracted on both
-    sides of the bra and in the ket, every integral against the oracle."""
-    p = W.class_problem(0, 0, lc, 70, 37, 3, 2, 2, box=8.0, exp_lo=0.05, exp_hi=1e4, seed=4200 + lc)
+@pytest.mark.parametrize("la,lb,lc", [(0, 0, 0), (0, 0, 4), (0, 0, 6), (1, 0, 0), (1, 0, 4), (0, 1, 2), (0, 1, 3)])
+def test_register_resident_classes_across_blocks(lx, la, lb, lc):
+    """(s s|C), (p s|C) and B-oriented (s p|C) run one thread per triple
+    (blocks of 128 and 64 triples): 70 pairs x 37 kets (2,590 triples, the
+    last block ragged), contracted on both sides of the bra and in the ket,
+    every integral against the oracle."""
+    p = W.class_problem(la, lb, lc, 70, 37, 3, 2, 2, box=8.0, exp_lo=0.05, exp_hi=1e4,
+                        seed=4200 + 10 * la + 5 * lb + lc)
     assert_parity(run(lx, p), p)
+    if la + lb:
+        assert_parity(run(lx, p, bra_pure=False), p, bra_pure=False)
 
 
 def test_ragged_and_single(lx):
