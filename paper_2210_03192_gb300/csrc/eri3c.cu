@@ -1170,7 +1170,8 @@ __global__ void __launch_bounds__(kSsThreads) eri3c_ss_dfj_kernel(const __grid_c
 }
 
 // (p s|C) classes, lc <= 4: la = 1, lb = 0 in the A orientation, or the
-// (s p|C) class run B-oriented (recurrences on the p shell, no HRR).  With
+// (s p|C) class run B-oriented (recurrences on the p shell, no HRR; its
+// descriptor holds the (p s|C) tables with orient = 1).  With
 // a = 1_i the n-quantum CVRR2 has two terms,
 //   (1_i 0|c) = (1_i 0)_{0,c} + c_i (0 0)_{1,c-1_i}    (Eq. cVRR2),
 // whose prerequisites are A_i(c) = sum [1_i 0|0]^(lc) X^c and
@@ -1588,9 +1589,12 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
       case 5: eri3c_ss_kernel<5><<<g, kSsThreads, 0, st>>>(d); break;
       default: eri3c_ss_kernel<6><<<g, kSsThreads, 0, st>>>(d); break;
     }
-  } else if ((d.digest == 0 || (d.digest == 1 && d.tiles)) && d.lc <= 4 &&
-             ((d.la == 1 && d.lb == 0 && d.orient == 0) || (d.la == 0 && d.lb == 1 && d.orient == 1))) {
-    // (p s|C) and B-oriented (s p|C), lc <= 4: register-resident
+  } else if ((d.digest == 0 || (d.digest == 1 && d.tiles)) && d.la == 1 && d.lb == 0 && d.lc <= 4 &&
+             (d.lc > 0 || d.K > 1)) {
+    // (p s|C) and B-oriented (s p|C) (whose descriptor holds the (p s|C)
+    // tables with orient = 1), 1 <= lc <= 4 or contracted: register-resident.
+    // (p s|s) with one primitive per triple stays on the tile kernel, which
+    // measured faster there.
     const long long items = d.digest ? d.ntiles : d.nsub * d.naux;
     const long long per = d.digest ? kPsThreads / 32 : kPsThreads;
     const unsigned g = (unsigned)std::min<long long>(std::max<long long>((items + per - 1) / per, 1), 152LL * 64);
