@@ -1565,6 +1565,19 @@ cudaError_t launch_aux_precompute(const DevBasis& aux, const int32_t* auxs, long
   return cudaGetLastError();
 }
 
+// SM count of the current device, for the grid-stride grids of the
+// register-resident kernels (read once; 152 on GB300).
+static int device_sms() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 152;
+    return v;
+  }();
+  return n;
+}
+
 cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
@@ -1579,7 +1592,7 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
   if (d.digest == 0 && d.la == 0 && d.lb == 0 && d.orient == 0) {
     // (s s|C): the register-resident form, one thread per triple
     const long long nb = (d.nsub * d.naux + kSsThreads - 1) / kSsThreads;
-    const unsigned g = (unsigned)std::min<long long>(std::max<long long>(nb, 1), 152LL * 32);
+    const unsigned g = (unsigned)std::min<long long>(std::max<long long>(nb, 1), (long long)device_sms() * 32);
     switch (d.lc) {
       case 0: eri3c_ss_kernel<0><<<g, kSsThreads, 0, st>>>(d); break;
       case 1: eri3c_ss_kernel<1><<<g, kSsThreads, 0, st>>>(d); break;
@@ -1597,7 +1610,7 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
     // measured faster there.
     const long long items = d.digest ? d.ntiles : d.nsub * d.naux;
     const long long per = d.digest ? kPsThreads / 32 : kPsThreads;
-    const unsigned g = (unsigned)std::min<long long>(std::max<long long>((items + per - 1) / per, 1), 152LL * 64);
+    const unsigned g = (unsigned)std::min<long long>(std::max<long long>((items + per - 1) / per, 1), (long long)device_sms() * 64);
     if (d.digest) {
       switch (d.lc) {
         case 0: eri3c_ps_dfj_kernel<0><<<g, kPsThreads, 0, st>>>(d); break;
@@ -1618,7 +1631,7 @@ cudaError_t launch_eri3c(const ClassDesc& d, int grid, cudaStream_t st) {
   } else if (d.digest == 1 && d.la == 0 && d.lb == 0 && d.orient == 0 && d.tiles) {
     // (s s|C) DF-J: one warp per tile
     const long long nb = (d.ntiles + kSsThreads / 32 - 1) / (kSsThreads / 32);
-    const unsigned g = (unsigned)std::min<long long>(std::max<long long>(nb, 1), 152LL * 32);
+    const unsigned g = (unsigned)std::min<long long>(std::max<long long>(nb, 1), (long long)device_sms() * 32);
     switch (d.lc) {
       case 0: eri3c_ss_dfj_kernel<0><<<g, kSsThreads, 0, st>>>(d); break;
       case 1: eri3c_ss_dfj_kernel<1><<<g, kSsThreads, 0, st>>>(d); break;
