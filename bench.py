@@ -246,7 +246,8 @@ def run_ours(args, rank, world, dist):
                launches=launches_per_step * args.steps,
                roofline=dict(bound="alu", achieved=round(ach, 2), peak=round(FP64_PEAK_GFLOPS, 1), unit="GFLOP/s",
                              frac=round(ach / FP64_PEAK_GFLOPS, 4), traffic=traffic,
-                             kernel="eri3c_kernel, class (%d%d|%d) K_ab=%d" % plans[dom]["cls"],
+                             kernel="%s, class (%d%d|%d) K_ab=%d" % ((kernel_name(plans[dom]["cls"]),)
+                                                                     + tuple(plans[dom]["cls"])),
                              peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                              flops_per_launch=plans[dom]["flops"], launch_ms=round(dms, 3)),
                l3_frac=dict(classes=len(l3), min=min(l3) if l3 else None,
@@ -261,6 +262,18 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return res
+
+
+def kernel_name(cls):
+    """The kernel a sweep class's launches run: the register-resident forms
+    for (s s|C) and for (p s|C) / (s p|C) with 1 <= lc <= 4 (or contracted),
+    the tile kernel otherwise."""
+    la, lb, lc, K = cls
+    if la == 0 and lb == 0:
+        return "eri3c_ss_kernel"
+    if la + lb == 1 and lc <= 4 and (lc > 0 or K > 1):
+        return "eri3c_ps_kernel"
+    return "eri3c_kernel"
 
 
 def run_e2e(plans, args):
