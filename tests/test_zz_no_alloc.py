@@ -57,7 +57,11 @@ def test_noalloc_matches_planned_path_three_calls_in_a_row():
     import paper_2210_03192_gb300 as lx
     cases = [W.class_problem(2, 3, 4, 7, 45, 3, 2, 1, box=6.0, exp_lo=0.1, exp_hi=50.0, seed=4242),
              W.class_problem(3, 1, 2, 5, 70, 2, 3, 2, box=6.0, exp_lo=0.1, exp_hi=50.0, seed=4343),
-             W.class_problem(2, 0, 3, 9, 33, 3, 1, 1, box=6.0, exp_lo=0.1, exp_hi=50.0, seed=4444)]
+             W.class_problem(2, 0, 3, 9, 33, 3, 1, 1, box=6.0, exp_lo=0.1, exp_hi=50.0, seed=4444),
+             # register-resident classes: (s s|d), and (s p|f) whose B-oriented
+             # list adds onto the A-oriented one
+             W.class_problem(0, 0, 2, 11, 50, 3, 2, 1, box=6.0, exp_lo=0.1, exp_hi=50.0, seed=4545),
+             W.class_problem(0, 1, 3, 11, 50, 3, 2, 1, box=6.0, exp_lo=0.05, exp_hi=1e4, seed=4646)]
     queued = [launch_noalloc(lx, p) for p in cases]  # back to back, no synchronisation in between
     torch.cuda.synchronize()
     got = [out.cpu().numpy() for out, _ in queued]
